@@ -1,0 +1,128 @@
+"""CPU oracle for greedy kNN-cost decimation (arXiv 2311.17604).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg may import this package; the library itself never does.
+
+``pd_oracle.c`` is the plain C definition (brute-force or kd-tree kNN plus a
+binary-heap sequential greedy); this module compiles it with gcc on first use
+and wraps it with ctypes.  ``slow.py`` holds a second, independent pure-numpy
+greedy that recomputes every cost from scratch at every step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BRUTE, KDTREE = 0, 1
+TERM_NONE, TERM_COLOR, TERM_ORIENT = 0, 1, 2
+D2_NONE = np.iinfo(np.int64).max
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP for the independent kNN queries).
+
+    ``-ffp-contract=off`` keeps every floating-point operation separately
+    rounded (no fused multiply-add), as the cost definition requires.
+    """
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            lib.orc_knn_cost.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, P, P, P]
+            lib.orc_knn_cost.restype = ctypes.c_int
+            lib.orc_decimate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P, P]
+            lib.orc_decimate.restype = ctypes.c_int
+            lib.orc_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(xyz, rgb, nrm, term):
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    assert xyz.ndim == 2 and xyz.shape[1] == 3
+    rgb = None if rgb is None else np.ascontiguousarray(rgb, dtype=np.uint8)
+    nrm = None if nrm is None else np.ascontiguousarray(nrm, dtype=np.float32)
+    if term == TERM_COLOR and rgb is None:
+        raise ValueError("colour term needs rgb")
+    if term == TERM_ORIENT and nrm is None:
+        raise ValueError("orientation term needs normals")
+    return xyz, rgb, nrm
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's parallel kNN loops use."""
+    return int(_load().orc_threads())
+
+
+def knn_cost(xyz, k, live=None, term=TERM_NONE, a=0.0, rgb=None, nrm=None, backend=KDTREE):
+    """k nearest live neighbours of every point and its cost (Eq. 10/11).
+
+    Returns (d2 [n,k] int64 ascending, idx [n,k] int32, cost [n] float64).
+    Missing neighbours are D2_NONE / -1.  Removed points get cost 0.
+    """
+    xyz, rgb, nrm = _prep(xyz, rgb, nrm, term)
+    n = xyz.shape[0]
+    lv = None if live is None else np.ascontiguousarray(live, dtype=np.uint8)
+    d2 = np.empty((n, k), dtype=np.int64)
+    idx = np.empty((n, k), dtype=np.int32)
+    cost = np.empty(n, dtype=np.float64)
+    rc = _load().orc_knn_cost(_ptr(xyz), _ptr(rgb), _ptr(nrm), n, _ptr(lv), k, term, a, backend,
+                              _ptr(d2), _ptr(idx), _ptr(cost))
+    if rc != 0:
+        raise ValueError("orc_knn_cost: invalid arguments")
+    return d2, idx, cost
+
+
+def decimate(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None, backend=KDTREE,
+             want_order=False):
+    """Sequential greedy decimation to exactly m points.
+
+    Returns keep (uint8 [n]); with ``want_order`` also the removal order and
+    the cost of each removed point at its removal (k = 1 density: d1^2).
+    """
+    xyz, rgb, nrm = _prep(xyz, rgb, nrm, term)
+    n = xyz.shape[0]
+    keep = np.empty(n, dtype=np.uint8)
+    order = np.empty(max(n - m, 0), dtype=np.int32) if want_order else None
+    pkey = np.empty(max(n - m, 0), dtype=np.float64) if want_order else None
+    req = ctypes.c_int64(0)
+    rc = _load().orc_decimate(_ptr(xyz), _ptr(rgb), _ptr(nrm), n, k, m, term, a, backend,
+                              _ptr(keep), _ptr(order), _ptr(pkey), ctypes.byref(req))
+    if rc != 0:
+        raise ValueError("orc_decimate: invalid arguments")
+    if want_order:
+        return keep, order, pkey
+    return keep
+
+
+def target_count(n: int, ratio: float) -> int:
+    """m = floor(ratio * n), computed in double (Eq. 1: lambda = m / |C|)."""
+    return int(np.floor(np.float64(ratio) * np.float64(n)))

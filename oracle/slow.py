@@ -1,0 +1,136 @@
+"""Second, independent CPU oracle: greedy decimation recomputed from scratch.
+
+TEST INFRASTRUCTURE ONLY.  Pure numpy / Python floats, no heap and no
+incremental updates: before every removal it recomputes, for every live point,
+the full sorted list of squared distances to the other live points and the
+cost from it, then removes the point with the largest (cost, index) key.
+It is quadratic per step, so it is meant for clouds of a few hundred points.
+
+Definitions followed (arXiv 2311.17604):
+  * Eq. 10 / Eq. 11: cost = sum over the k nearest of 1 / d^2, summed in
+    ascending-distance order in binary64; k = 1 density-only compares d1^2 as
+    integers.
+  * Greedy removal of the highest cost (section "Computing per-sample costs"),
+    larger index first among equal costs.
+  * Optional neighbour weights for the orientation term (Eq. 13, read with an
+    absolute value because estimated normals are unoriented) and the colour
+    term (no formula printed in the paper; this library's reading).
+Also here: an exhaustive enumerator of removal orders for tiny inputs and the
+Eq. 2 optimum (largest achievable minimum spacing) by brute force.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+TERM_NONE, TERM_COLOR, TERM_ORIENT = 0, 1, 2
+
+
+def _weight(term, a, rgb, nrm, p, q):
+    if term == TERM_COLOR:
+        dr = float(rgb[p, 0]) - float(rgb[q, 0])
+        dg = float(rgb[p, 1]) - float(rgb[q, 1])
+        db = float(rgb[p, 2]) - float(rgb[q, 2])
+        s = dr * dr
+        s = s + dg * dg
+        s = s + db * db
+        return 1.0 - a * (math.sqrt(s) / (255.0 * math.sqrt(3.0)))
+    if term == TERM_ORIENT:
+        d = float(nrm[p, 0]) * float(nrm[q, 0])
+        d = d + float(nrm[p, 1]) * float(nrm[q, 1])
+        d = d + float(nrm[p, 2]) * float(nrm[q, 2])
+        return 1.0 - a * (1.0 - abs(d))
+    return 1.0
+
+
+def keys_from_scratch(xyz, live, k, term=TERM_NONE, a=0.0, rgb=None, nrm=None):
+    """Key of every live point computed from scratch.
+
+    Returns a list of (primary, index) tuples (None for removed points) whose
+    Python tuple order is the removal order: the larger key goes first.
+    primary is -d1^2 for the k = 1 density cost (an exact integer) and the
+    binary64 cost otherwise.
+    """
+    xyz = np.asarray(xyz, dtype=np.int64)
+    ids = np.nonzero(live)[0]
+    keys = [None] * len(xyz)
+    for p in ids:
+        others = ids[ids != p]
+        d = xyz[others] - xyz[p]
+        d2 = (d * d).sum(axis=1)
+        # ascending (d2, index) order; equal distances sort by index
+        order = np.lexsort((others, d2))[:k]
+        if k == 1 and term == TERM_NONE:
+            prim = -int(d2[order[0]]) if len(order) else -(1 << 62)
+        else:
+            c = 0.0
+            for j in order:
+                w = _weight(term, a, rgb, nrm, p, int(others[j]))
+                dd = float(d2[j])
+                c = c + (w / dd if dd != 0.0 else math.inf)
+            prim = c
+        keys[p] = (prim, int(p))
+    return keys
+
+
+def greedy_from_scratch(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None):
+    """Remove the max-key live point until m remain; returns (keep, order)."""
+    n = len(xyz)
+    live = np.ones(n, dtype=bool)
+    order = []
+    while live.sum() > m:
+        keys = keys_from_scratch(xyz, live, k, term, a, rgb, nrm)
+        best = max(kk for kk in keys if kk is not None)
+        live[best[1]] = False
+        order.append(best[1])
+    return live.astype(np.uint8), order
+
+
+def greedy_orders_exhaustive(xyz, k, m):
+    """All removal sequences of length n - m whose every step removes the key max.
+
+    Enumerates every ordered sequence of distinct points and keeps those in
+    which each removed point holds the largest key among the live points at
+    that step.  The greedy's tie-break makes keys distinct, so exactly one
+    sequence must qualify.
+    """
+    n = len(xyz)
+    good = []
+    for seq in itertools.permutations(range(n), n - m):
+        live = np.ones(n, dtype=bool)
+        ok = True
+        for p in seq:
+            keys = keys_from_scratch(xyz, live, k)
+            if max(kk for kk in keys if kk is not None)[1] != p:
+                ok = False
+                break
+            live[p] = False
+        if ok:
+            good.append(list(seq))
+    return good
+
+
+def min_spacing2(xyz, sel=None):
+    """Smallest squared distance between two selected points (Eq. 2 objective)."""
+    x = np.asarray(xyz, dtype=np.int64)
+    if sel is not None:
+        x = x[np.asarray(sel, dtype=bool)]
+    if len(x) < 2:
+        return math.inf
+    d = x[:, None, :] - x[None, :, :]
+    d2 = (d * d).sum(axis=2)
+    np.fill_diagonal(d2, np.iinfo(np.int64).max)
+    return int(d2.min())
+
+
+def best_spacing2(xyz, m):
+    """Eq. 2 optimum by brute force: max over |C'| = m of the min squared spacing."""
+    n = len(xyz)
+    best = -1
+    for sub in itertools.combinations(range(n), m):
+        sel = np.zeros(n, dtype=bool)
+        sel[list(sub)] = True
+        best = max(best, min_spacing2(xyz, sel))
+    return best

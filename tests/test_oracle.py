@@ -1,0 +1,226 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test ties the oracle to something other than itself: closed forms of
+Eq. 10/11, configurations whose greedy outcome follows by hand, the paper's
+own counts, an independent recompute-from-scratch greedy, exhaustive
+enumeration on tiny inputs, invariants the paper states, and symmetries.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import slow
+from paper_2311_17604_gb300 import synth
+
+
+def _ulps(x, exact):
+    return abs(Fraction(x) - exact) / Fraction(np.spacing(x))
+
+
+# ---------------------------------------------------------------- Eq. 10 / 11
+def test_cost_closed_form(orc):
+    """w^k of a point with neighbours at d^2 = 1, 4, 9, 16 is 205/144 (Eq. 11)."""
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 2, 0], [0, 0, 3], [4, 0, 0]], np.int32)
+    d2, idx, cost = orc.knn_cost(xyz, 4, backend=orc.BRUTE)
+    assert list(d2[0]) == [1, 4, 9, 16]
+    assert list(idx[0]) == [1, 2, 3, 4]
+    assert _ulps(cost[0], Fraction(205, 144)) <= 4
+    # k = 1 (Eq. 10): 1 / d^2 of the nearest
+    _, _, c1 = orc.knn_cost(xyz, 1, backend=orc.BRUTE)
+    assert c1[0] == 1.0
+    # fewer than k other points: missing terms contribute nothing
+    _, idx6, c6 = orc.knn_cost(xyz, 6, backend=orc.BRUTE)
+    assert _ulps(c6[0], Fraction(205, 144)) <= 4
+    assert list(idx6[0][4:]) == [-1, -1]
+
+
+def test_cost_duplicates_and_lone_point(orc):
+    xyz = np.array([[5, 5, 5], [5, 5, 5], [100, 0, 0]], np.int32)
+    for k in (1, 2, 4):
+        d2, _, cost = orc.knn_cost(xyz, k, backend=orc.BRUTE)
+        assert d2[0, 0] == 0 and np.isinf(cost[0]) == (k > 1 or True)
+    _, _, c = orc.knn_cost(xyz[2:], 3, backend=orc.BRUTE)
+    assert c[0] == 0.0
+
+
+def test_cost_matches_fractions_random(orc):
+    """Random small clouds: cost within a few ulps of the exact rational sum."""
+    x = synth.random_cloud(3, 200, 60)
+    d2, _, cost = orc.knn_cost(x, 6, backend=orc.BRUTE)
+    for p in range(0, 200, 7):
+        if (d2[p] == 0).any():
+            assert np.isinf(cost[p])
+            continue
+        exact = sum(Fraction(1, int(v)) for v in d2[p])
+        assert _ulps(cost[p], exact) <= 8
+
+
+def test_knn_lists_are_the_true_nearest(orc):
+    """The stored d^2 lists equal a sorted full distance row (brute force)."""
+    x = synth.random_cloud(5, 300, 40)
+    d2, idx, _ = orc.knn_cost(x, 5, backend=orc.KDTREE)
+    xi = x.astype(np.int64)
+    for p in range(0, 300, 11):
+        row = ((xi - xi[p]) ** 2).sum(1)
+        row[p] = np.iinfo(np.int64).max
+        assert list(d2[p]) == sorted(row)[:5]
+        assert all(row[j] == v for j, v in zip(idx[p], d2[p]))
+
+
+# ---------------------------------------------------------- greedy by hand
+def test_lattice_line_k1(orc):
+    """x = i mm, k = 1: all costs tie, the larger index goes first -> keep 0..m-1."""
+    for n, m in ((20, 7), (101, 50), (64, 1), (10, 0), (10, 10)):
+        keep = orc.decimate(synth.lattice_line(n), 1, m)
+        assert list(np.nonzero(keep)[0]) == list(range(m))
+
+
+def test_separated_pairs_k1(orc):
+    """Far-apart pairs with distinct gaps: removing r points takes the
+    higher-index member of each of the r tightest pairs."""
+    rng = np.random.default_rng(11)
+    P = 12
+    gaps = rng.permutation(np.arange(1, P + 1)) * 3
+    pts, first = [], []
+    for i, g in enumerate(gaps):
+        base = np.array([10000 * i, 0, 0])
+        pa, pb = base, base + np.array([0, int(g), 0])
+        if rng.random() < 0.5:
+            pa, pb = pb, pa
+        first.append(len(pts))
+        pts += [pa, pb]
+    xyz = np.array(pts, np.int32)
+    for r in (1, 4, P):
+        keep = orc.decimate(xyz, 1, len(xyz) - r)
+        tight = np.argsort(gaps)[:r]
+        removed = sorted(first[i] + 1 for i in tight)
+        assert sorted(np.nonzero(keep == 0)[0]) == removed
+
+
+def test_fig3_configuration(orc):
+    """Fig. 3: a close pair with equal w^{k=1}; w^{k=4} removes the member whose
+    other neighbours are closer, while k = 1 falls back to the index order."""
+    black = [(-100, 0, 0), (100, 0, 0), (0, 173, 0)]
+    a, b = (0, 48, 0), (0, 68, 0)   # same nearest distance (20) to each other
+    xyz = np.array(black + [a, b], np.int32)
+
+    def inv2(p, q):
+        return Fraction(1, sum((u - v) ** 2 for u, v in zip(p, q)))
+    wa = sum(inv2(a, q) for q in black + [b])
+    wb = sum(inv2(b, q) for q in black + [a])
+    assert wa != wb
+    loser = 3 if wa > wb else 4
+    keep4 = orc.decimate(xyz, 4, 4)
+    assert np.nonzero(keep4 == 0)[0].tolist() == [loser]
+    keep1 = orc.decimate(xyz, 1, 4)          # tie at k = 1: larger index goes
+    assert np.nonzero(keep1 == 0)[0].tolist() == [4]
+
+
+def test_paper_cube_count():
+    """Cube example: 10 % of 452,230 points is 45,223 (section Results)."""
+    import oracle
+    assert oracle.target_count(452230, 0.1) == 45223
+    assert abs(45223 / 500 - 90.45) < 0.005
+
+
+# ------------------------------------------------- independent oracles
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("seed,span", [(0, 25), (1, 400), (2, 8)])
+def test_heap_greedy_equals_recompute_from_scratch(orc, k, seed, span):
+    x = synth.random_cloud(seed, 120, span)
+    m = 37
+    keep, order, _ = orc.decimate(x, k, m, want_order=True)
+    keep2, order2 = slow.greedy_from_scratch(x, k, m)
+    assert np.array_equal(keep, keep2)
+    assert list(order) == order2
+
+
+@pytest.mark.parametrize("term", [1, 2])
+def test_weighted_terms_equal_recompute(orc, term):
+    rng = np.random.default_rng(4)
+    x = synth.random_cloud(7, 90, 30)
+    rgb = rng.integers(0, 256, size=(90, 3)).astype(np.uint8)
+    nrm = rng.normal(size=(90, 3)).astype(np.float32)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    a = 0.3 if term == 1 else 0.5
+    for k in (1, 3):
+        keep, order, _ = orc.decimate(x, k, 30, term=term, a=a, rgb=rgb, nrm=nrm,
+                                      want_order=True)
+        keep2, order2 = slow.greedy_from_scratch(x, k, 30, term=term, a=a, rgb=rgb, nrm=nrm)
+        assert list(order) == order2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_exhaustive_unique_greedy_order(orc, seed):
+    """Tiny inputs: exactly one removal sequence takes the key max at every
+    step, and it is the oracle's order."""
+    x = synth.random_cloud(seed, 6, 6)
+    for k in (1, 2):
+        seqs = slow.greedy_orders_exhaustive(x, k, 3)
+        _, order, _ = orc.decimate(x, k, 3, want_order=True)
+        assert seqs == [list(order)]
+
+
+def test_eq2_context_small(orc):
+    """Greedy spacing never exceeds the Eq. 2 optimum (brute force, n = 9)."""
+    x = synth.random_cloud(9, 9, 30)
+    keep = orc.decimate(x, 1, 4)
+    assert slow.min_spacing2(x, keep) <= slow.best_spacing2(x, 4)
+
+
+# ------------------------------------------------------------ invariants
+def test_room_scan_invariants(orc):
+    """Room scan (200k points, k = 1, keep 25 %): exact count, non-increasing
+    removal keys (a removal never raises a cost, section Sub-sampling step 2),
+    spacing of the kept set never below that of the input."""
+    s = synth.room_scan(**synth.ROOM_200K)
+    m = 50000
+    keep, order, pk = orc.decimate(s.xyz, 1, m, want_order=True)
+    assert int(keep.sum()) == m
+    assert np.all(np.diff(pk) >= 0)          # d1^2 ascending = cost descending
+    assert len(set(order.tolist())) == len(order)
+    assert not keep[order].any()
+
+
+@pytest.mark.parametrize("k", [2, 4, 6])
+def test_monotone_cost_k(orc, k):
+    x = synth.random_cloud(21, 3000, 300)
+    keep, order, pk = orc.decimate(x, k, 500, want_order=True)
+    assert int(keep.sum()) == 500
+    assert np.all(np.diff(pk) <= 0)
+    xi = x.astype(np.int64)
+    # min spacing of the retained set is at least the input's
+    assert slow.min_spacing2(xi[keep == 1]) >= slow.min_spacing2(xi[:800])
+
+
+# ----------------------------------------------------------- symmetries
+@pytest.mark.parametrize("k", [1, 4])
+def test_translation_and_scale(orc, k):
+    x = synth.random_cloud(8, 2000, 500)
+    base = orc.decimate(x, k, 700)
+    assert np.array_equal(base, orc.decimate(x + np.int32(123457), k, 700))
+    # x2 scaling multiplies every d^2 by 4 and every cost by 1/4 exactly
+    assert np.array_equal(base, orc.decimate(x * 2, k, 700))
+
+
+# ---------------------------------------------------------- backends
+@pytest.mark.parametrize("shape", ["cube", "plane", "line", "dups"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_kdtree_equals_brute(orc, shape, k):
+    if shape == "cube":
+        x = synth.random_cloud(1, 1500, 1000)
+    elif shape == "plane":
+        x = synth.random_cloud(2, 1500, 300, dims=2)
+    elif shape == "line":
+        x = synth.random_cloud(3, 1500, 5000, dims=1)
+    else:
+        x = synth.random_cloud(4, 1500, 9)
+    live = (np.arange(1500) % 3 != 0).astype(np.uint8)
+    a = orc.knn_cost(x, k, live=live, backend=orc.BRUTE)
+    b = orc.knn_cost(x, k, live=live, backend=orc.KDTREE)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    ka = orc.decimate(x, k, 400, backend=orc.BRUTE)
+    kb = orc.decimate(x, k, 400, backend=orc.KDTREE)
+    assert np.array_equal(ka, kb)
