@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: greedy kNN-cost decimation throughput on one GB300.
+
+A step decimates one synthetic terrestrial-LiDAR scan end to end on the
+device: voxel-grid build (Morton radix sort, octree cell table), the first
+k-nearest-neighbour/cost pass, the removal rounds and the keep mask.  The
+default workload is the 10000 x 2000-ray outdoor scan (ground plane, 40 boxes,
+20 spheres at 1-60 m, 15 % dropout, int32 mm) with the k = 4 density cost,
+keeping 10 % of the points.
+
+  value   input points / second of device time, inputs resident in HBM
+  e2e     the same through pd_decimate_host (host buffers, copies timed)
+  roofline  the first full kNN/cost pass: algorithmic bytes / launch time
+  cpu_baseline  the CPU oracle on a bounded sector of the same scan
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+       python bench.py --impl reference ...   (the CPU oracle as the reference arm)
+Multi-GPU (torchrun): every rank decimates its own scan (seed + rank), no
+collective on the data path ("weak" scaling); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2311_17604_gb300 import synth  # noqa: E402
+
+METRIC = "decimated points/sec/GB300 (oracle-exact), % of HBM roofline; batched p99 ms"
+UNIT = "points/s"
+
+WORKLOADS = {
+    "outdoor": dict(desc="outdoor single-station scan, 10000x2000 rays, 15% dropout, "
+                         "ground + 40 boxes + 20 spheres at 1-60 m, int32 mm; k=4; keep 10%",
+                    gen=lambda seed: synth.outdoor_scan(seed=seed, n_az=10000, n_el=2000),
+                    k=4, ratio=0.1, sample=400_000, ref_sample=150_000),
+    "room": dict(desc="room single-station scan, 1000x200 rays, 10x8x3 m, 3 boxes, "
+                      "2 mm noise, int32 mm; k=1; keep 25%",
+                 gen=lambda seed: synth.room_scan(seed=seed, n_az=1000, n_el=200),
+                 k=1, ratio=0.25, sample=200_000, ref_sample=200_000),
+}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def aggregate(local_seconds: float, local_units: int, dist=None):
+    """Whole-job numbers: units summed over ranks, time = max over ranks."""
+    if dist is None:
+        return local_seconds, local_units
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
+def oracle_sample(scan_xyz, n_sample, k, ratio):
+    """The oracle as it stands on the first n_sample points (an azimuth sector)."""
+    import oracle
+    x = np.ascontiguousarray(scan_xyz[:n_sample])
+    m = oracle.target_count(len(x), ratio)
+    t0 = time.perf_counter()
+    oracle.decimate(x, k, m)
+    dt = time.perf_counter() - t0
+    return len(x), dt, oracle.threads()
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, wl, rank):
+    """CPU oracle on bounded samples of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    scan = wl["gen"](0)
+    ns = min(wl["ref_sample"], scan.n)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    times = []
+    threads = 1
+    for _ in range(args.steps):
+        n, dt, threads = oracle_sample(scan.xyz, ns, wl["k"], wl["ratio"])
+        times.append(dt)
+    tot = sum(times)
+    value = ns * len(times) / tot
+    sample = "first %d points (azimuth sector) of the %d-point scan, k=%d, keep %g" % (
+        ns, scan.n, wl["k"], wl["ratio"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["desc"], "sample_points": ns},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, wl, rank, world, local_rank, dist):
+    import torch
+
+    from paper_2311_17604_gb300 import build
+    build.build()
+    import paper_2311_17604_gb300.pd as pd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scan = wl["gen"](rank)
+    n, k = scan.n, wl["k"]
+    import oracle
+    m = oracle.target_count(n, wl["ratio"])
+    xyz_dev = torch.from_numpy(scan.xyz).to(dev)
+    ctx = pd.Context()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    L = pd.lib()
+    L.pd__launch_count.restype = ctypes.c_longlong
+
+    def step():
+        g = pd.Grid(ctx, xyz_dev, stream=stream)
+        keep = pd.pd_decimate_count(g, m, k=k, stream=stream)
+        st = g.stats()
+        g.free()
+        return keep, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = L.pd__launch_count()
+    step_ms, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)                       # evict L2 between timed steps
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        keep, st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = L.pd__launch_count() - launches0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    assert int(keep.sum().item()) == m
+    tot_s, units = aggregate(sum(step_ms) / 1e3, n * args.steps, dist)
+    value = units / tot_s
+
+    # e2e: the host C-ABI entry with pinned buffers, copies inside the timed region
+    xyz_pin = torch.from_numpy(scan.xyz).pin_memory()
+    keep_pin = torch.empty(n, dtype=torch.uint8).pin_memory()
+    xyz_np, keep_np = xyz_pin.numpy(), keep_pin.numpy()
+    pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)   # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)
+    e2e_s, e2e_units = aggregate(time.perf_counter() - t0, n * args.steps, dist)
+
+    # roofline of the first full kNN/cost pass (one launch per step): algorithmic
+    # bytes = per query 16 B read ({x,y,z,index}) + written key 8 + k-th d^2 8 +
+    # flags 1 + S stored neighbours x 4
+    S = 8 if (k == 1 or k + 1 > 4) else 4
+    if k + 1 > 8:
+        S = 17
+    per_q = 16 + 8 + 8 + 1 + 4 * S
+    ms_first = statistics.mean(s["ms_knn_first"] for s in stats)
+    q_first = statistics.mean(s["q_first"] for s in stats)
+    peak, peak_kind = measured_peaks()
+    achieved = q_first * per_q / (ms_first / 1e3) / 1e9
+    traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "knn_kernel (first pass)",
+                "bytes_per_query": per_q, "queries": q_first, "ms": ms_first,
+                "peak_kind": peak_kind}
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ns = min(wl["sample"], n)
+        nsmp, dt, threads = oracle_sample(scan.xyz, ns, k, wl["ratio"])
+        cpu = {"value": nsmp / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "first %d points (azimuth sector) of the scan, k=%d, keep %g; kNN "
+                         "on %d threads, greedy single-threaded; %.1f s"
+                         % (nsmp, k, wl["ratio"], threads, dt)}
+    mean = {key: statistics.mean(s[key] for s in stats) for key in stats[0]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": m, "k": k,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MiB buffer written between timed steps; working set > L2"},
+            "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
+                    "d2h_bytes_per_step": n},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": int(launches),
+            "detail": {"rounds": mean["rounds"], "ms_knn": mean["ms_knn"],
+                       "ms_build": mean["ms_build"], "ms_rules": mean["ms_rules"],
+                       "ms_decimate": mean["ms_total"], "requeries": mean["requeries"],
+                       "filtered_queries": mean["filtered_queries"],
+                       "danger_queries": mean["danger_queries"],
+                       "dup_removed": mean["dup_removed"], "step_ms": step_ms}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="outdoor", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_gpu(args, wl, rank, world, local_rank, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * pd.h -- C ABI of libpd: greedy kNN-cost point-cloud decimation on one GPU.
+ *
+ * Method: Comino-Trinidad, Chica, Andujar, "Revisiting Poisson-disk
+ * Subsampling for Massive Point Cloud Decimation" (arXiv 2311.17604).
+ *
+ *   Problem (Eq. 1): given a cloud C and a target count m, keep a subset
+ *   C' of C with |C'| = m whose local densities are as even as possible.
+ *   Cost of a point p (Eq. 10 for k = 1, Eq. 11 for k >= 2):
+ *       w_p^k = sum over the k nearest other live points p' of 1 / d(p,p')^2
+ *   Greedy (section "Computing per-sample costs", section "Sub-sampling
+ *   algorithm"): repeatedly remove the point of largest cost -- among equal
+ *   costs the larger input index first -- and update the costs of the points
+ *   that had it among their k nearest neighbours, until m points remain.
+ *
+ * The library reproduces the sequential greedy result exactly (same retained
+ * index set) for the density cost, with all work in CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *   - Points are int32 millimetre coordinates, n x 3 row-major (x, y, z).
+ *     Their spread per axis must stay below 2^25 mm so every squared distance
+ *     (below 3 * 2^50) is exact in an int64 and in a binary64.
+ *   - "_dev" pointers are device memory owned by the caller; the library
+ *     never frees them.  "_host" pointers are host memory owned by the caller.
+ *   - Output arrays are indexed by the caller's input order.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     ordered on that stream.  Documented host synchronisations:
+ *     pd_build_grid (reads back the cloud's extent and the cell count),
+ *     pd_decimate_* (reads back counters once per removal round and waits for
+ *     the result before returning).
+ *   - All library-owned device memory comes from the allocator given to
+ *     pd_ctx_create (stream-ordered on the call's stream), or from
+ *     cudaMallocAsync when none is given.
+ *   - Every call returns PD_OK or an error code and never aborts the process;
+ *     pd_last_error() returns a description of the last failure on a context.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PD_OK 0
+#define PD_EINVAL 1    /* invalid argument (NULL pointer, n < 1, m outside [0,n], k outside [1,16]) */
+#define PD_ERANGE 2    /* coordinate spread >= 2^25 mm on some axis */
+#define PD_ENOMEM 3    /* the allocator returned NULL */
+#define PD_ECUDA 4     /* a CUDA runtime call failed */
+#define PD_ETIMEOUT 5  /* a device-side bounded wait gave up */
+#define PD_EINTERNAL 6 /* an internal consistency check failed (no progress) */
+
+/* neighbour-weight terms (section "Additional cost terms") */
+#define PD_TERM_NONE 0
+#define PD_TERM_COLOR 1  /* w = 1 - weight * ||rgb_p - rgb_q||_2 / (255 sqrt 3) */
+#define PD_TERM_ORIENT 2 /* w = 1 - weight * (1 - |n_p . n_q|)   (Eq. 13)      */
+
+#define PD_KMAX 16
+
+typedef struct pd_ctx pd_ctx;   /* allocator, last error, tuning cache */
+typedef struct pd_grid pd_grid; /* one resident cloud: sorted points, cell table, state */
+
+/* Stream-ordered allocator callbacks (e.g. a framework's caching allocator). */
+typedef struct {
+    void* (*alloc)(void* user, size_t bytes, void* stream); /* NULL on failure */
+    void (*free)(void* user, void* ptr, void* stream);
+    void* user;
+} pd_allocator;
+
+typedef struct {
+    int32_t leaf_max;   /* most points per octree leaf cell, 4..32 (0 = 32) */
+    int32_t reserved[7];
+} pd_grid_params;
+
+typedef struct {
+    int32_t k;                /* neighbours in the cost, 1..PD_KMAX (Eq. 11) */
+    int32_t term;             /* PD_TERM_* */
+    double weight;            /* weight of the colour / orientation term */
+    const float* normals_dev; /* n x 3 float32, input order (PD_TERM_ORIENT) */
+    double band;              /* k >= 2: fraction of live points examined per
+                                 removal round (0 = default 0.2); never
+                                 changes the result */
+    int32_t reserved[6];
+} pd_cost_params;
+
+typedef struct {
+    int64_t n, m;
+    int32_t rounds;           /* removal rounds after duplicate removal */
+    int32_t grid_builds;      /* cell-table (re)builds during decimation */
+    int64_t dup_removed;      /* points removed in the duplicate phase */
+    int64_t requeries;        /* neighbour searches after the first pass */
+    int64_t filtered_queries; /* k >= 2 invariance searches */
+    int64_t danger_queries;   /* k >= 2 protected-radius searches */
+    double ms_total;          /* device time of the last pd_decimate_* call */
+    double ms_knn;            /* of which: all neighbour searches */
+    double ms_build;          /* of which: cell-table rebuilds */
+    double ms_knn_first;      /* the first full neighbour pass (one launch) */
+    int64_t q_first;          /* queries of that pass */
+    double ms_knn_requery;    /* re-searches of points that lost a neighbour */
+    double ms_rules;          /* removal-rule kernels and key selection */
+    int64_t launches;         /* kernels launched by the call */
+} pd_stats;
+
+/* Context: owns nothing but the allocator hooks, the error string and caches. */
+int pd_ctx_create(const pd_allocator* alloc /* may be NULL */, pd_ctx** out);
+void pd_ctx_destroy(pd_ctx* ctx);
+const char* pd_strerror(int code);
+const char* pd_last_error(const pd_ctx* ctx);
+
+/*
+ * Build the voxel grid of a cloud (section "Sub-sampling algorithm": the
+ * paper voxelises the cloud; here one Morton-order radix sort yields cells of
+ * every power-of-two size, an adaptive leaf level per point, and a hashed
+ * table of cell ranges).
+ *   xyz_dev  n x 3 int32, device.  Copied; may be freed after the call.
+ *   rgb_dev  n x 3 uint8, device, or NULL (needed for PD_TERM_COLOR).  Copied.
+ *   params   may be NULL.
+ * Synchronises the stream once (extent and cell count).
+ */
+int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t* rgb_dev, int64_t n,
+                  const pd_grid_params* params, void* stream, pd_grid** out);
+int pd_grid_free(pd_grid* grid);
+
+/*
+ * Cost of every point of the full cloud (Eq. 10 / Eq. 11, optional weights).
+ *   cost_dev  n doubles (may be NULL): binary64 sum over the k nearest, in
+ *             ascending-distance order; 1/d^2 for k = 1; +inf if a neighbour
+ *             coincides; 0 for a cloud of one point.
+ *   knn_dev   n x k int32 input indices of the k nearest, ascending (d^2,
+ *             tie order unspecified), -1 where fewer exist.  May be NULL.
+ */
+int pd_knn_cost(pd_grid* grid, const pd_cost_params* cp, double* cost_dev, int32_t* knn_dev,
+                void* stream);
+
+/*
+ * Greedy decimation to exactly m points (Eq. 1, |C'| = m).
+ *   keep_dev  n bytes: 1 = retained, 0 = removed, input order.
+ * The grid's point state is consumed: build a new grid to decimate again.
+ * Density-only costs give the sequential greedy's exact result.
+ */
+int pd_decimate_count(pd_grid* grid, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev,
+                      void* stream);
+/* Same with m = floor(ratio * n) computed in binary64 (lambda = m / |C|). */
+int pd_decimate_ratio(pd_grid* grid, const pd_cost_params* cp, double ratio, uint8_t* keep_dev,
+                      void* stream);
+/* Counters of the last pd_decimate_* call on this grid. */
+int pd_grid_stats(const pd_grid* grid, pd_stats* out);
+
+/*
+ * End-to-end call on host buffers: copy xyz (and rgb / normals) to the device,
+ * build the grid, decimate to m points and copy the keep mask back.
+ *   xyz_host n x 3 int32; rgb_host n x 3 uint8 or NULL; normals_host n x 3
+ *   float32 or NULL (used when cp->term == PD_TERM_ORIENT); keep_host n bytes.
+ * Synchronises the stream before returning.
+ */
+int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_host,
+                     const float* normals_host, int64_t n, const pd_cost_params* cp, int64_t m,
+                     uint8_t* keep_host, void* stream, pd_stats* stats /* may be NULL */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

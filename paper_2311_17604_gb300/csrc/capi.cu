@@ -1,0 +1,1067 @@
+// capi.cu -- the C ABI of libpd (pd.h): contexts, grids, decimation driver.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/pd.h"
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+using namespace pd;
+
+namespace pd {
+long long g_launch_count = 0;
+}
+
+namespace pd {
+// launchers defined in rounds.cu
+cudaError_t launch_dup_flag(const u64*, const int4*, int64_t, uint8_t*, unsigned long long*,
+                            cudaStream_t);
+cudaError_t launch_dup_remove(const uint8_t*, const int4*, int64_t, int, uint8_t*, cudaStream_t);
+cudaError_t launch_sel_hist(const u64*, const uint8_t*, int64_t, const u64*, const int*, int64_t,
+                            int, const uint32_t*, uint32_t*, cudaStream_t);
+cudaError_t launch_sel_compact(const u64*, const int4*, const uint8_t*, int64_t, const u64*,
+                               const int*, int64_t, int, const uint32_t*, u64*, int*, int*,
+                               cudaStream_t);
+cudaError_t launch_k1_cand(const u64*, const int4*, const uint8_t*, const int*, const uint8_t*,
+                           int64_t, int, u64, int, uint8_t*, int*, int*, int*, int*, cudaStream_t);
+cudaError_t launch_k1_slow(const GridView&, const u64*, const uint8_t*, const u64*, const int*,
+                           const int*, int, uint8_t*, int*, int*, cudaStream_t);
+cudaError_t launch_k1_fix(const int*, const int*, int, const int4*, const int*, int,
+                          const uint8_t*, uint8_t*, int*, cudaStream_t);
+cudaError_t launch_kk_cand(const u64*, const int4*, const uint8_t*, const int*, const uint8_t*,
+                           int64_t, int, int, u64, int, uint8_t*, int*, int*, uint8_t*, uint8_t*,
+                           cudaStream_t);
+cudaError_t launch_kk_accept(const int*, const int*, int, const u64*, const u64*, uint8_t*, int*,
+                             int*, cudaStream_t);
+cudaError_t launch_danger(const GridView&, const int*, const int*, int, const u64*,
+                          const uint8_t*, const uint8_t*, uint8_t*, const u64*, int, int2*, int*,
+                          int, int*, cudaStream_t);
+cudaError_t launch_accept_above(const u64*, const int4*, const uint8_t*, int64_t, u64, int,
+                                uint8_t*, int*, int*, cudaStream_t);
+cudaError_t launch_pair_fix(const int2*, const int*, int, int, const uint8_t*, uint8_t*, int*,
+                            cudaStream_t);
+cudaError_t launch_remove(const int*, const int*, int, uint8_t*, uint8_t*, uint8_t*,
+                          unsigned long long*, cudaStream_t);
+cudaError_t launch_dirty(const uint8_t*, const int*, int64_t, int, int, uint8_t*, cudaStream_t);
+cudaError_t launch_keep(const int4*, const uint8_t*, int64_t, uint8_t*, cudaStream_t);
+cudaError_t launch_knn_out(const int4*, const double*, const int*, int64_t, int, int, double*,
+                           int32_t*, cudaStream_t);
+cudaError_t launch_newpos(const int*, int64_t, int*, cudaStream_t);
+cudaError_t launch_remap(const int*, int64_t, const int*, int*, const int*, int64_t, int,
+                         cudaStream_t);
+cudaError_t launch_take_u64(const int*, int64_t, const u64*, u64*, cudaStream_t);
+cudaError_t launch_take_i4(const int*, int64_t, const int4*, int4*, cudaStream_t);
+cudaError_t launch_take_u8(const int*, int64_t, const uint8_t*, uint8_t*, cudaStream_t);
+cudaError_t launch_take_uc4(const int*, int64_t, const uchar4*, uchar4*, cudaStream_t);
+cudaError_t launch_take_f4(const int*, int64_t, const float4*, float4*, cudaStream_t);
+}  // namespace pd
+
+// ============================================================ context
+struct pd_ctx {
+    pd_allocator alloc;
+    int has_alloc;
+    char err[512];
+};
+
+static void set_err(pd_ctx* c, const char* fmt, const char* a = "", long long b = 0) {
+    if (c) snprintf(c->err, sizeof(c->err), fmt, a, b);
+}
+
+static void* ctx_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->has_alloc) return c->alloc.alloc(c->alloc.user, bytes, (void*)st);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+static void ctx_free(pd_ctx* c, void* p, cudaStream_t st) {
+    if (!p) return;
+    if (c->has_alloc) c->alloc.free(c->alloc.user, p, (void*)st);
+    else cudaFreeAsync(p, st);
+}
+
+// ============================================================ grid
+struct pd_grid {
+    pd_ctx* ctx;
+    cudaStream_t st;
+    int64_t n;   // input points
+    int64_t ng;  // points held by the grid arrays
+    int B, shift, T;
+    int3 origin, umax;
+    int4* pos;
+    u64* code;
+    uint8_t* leaf;
+    uint8_t* alive;
+    uchar4* rgb;
+    float4* nrm;
+    HashSlot* hash;
+    u64 hmask;
+    int4* groups;
+    int ngroups;
+    // neighbour state
+    int S, k, density_k1;
+    u64* prim;
+    int* nbr;
+    u64* rk2;
+    uint8_t* flg;
+    // small device scalars
+    int* d_int;                  // [0] ngroups, [1..7] counters
+    unsigned long long* d_u64;   // [0] counts
+    std::vector<void*> owned;
+    pd_stats stats;
+    int trace;  // PD_TRACE set: one line per removal round on stderr
+};
+
+namespace {
+
+void* scratch_alloc(void* self, size_t bytes) {
+    pd_grid* g = (pd_grid*)self;
+    return ctx_alloc(g->ctx, bytes, g->st);
+}
+void scratch_free(void* self, void* p) {
+    pd_grid* g = (pd_grid*)self;
+    ctx_free(g->ctx, p, g->st);
+}
+Scratch scratch_of(pd_grid* g) {
+    Scratch s;
+    s.alloc = scratch_alloc;
+    s.free = scratch_free;
+    s.self = g;
+    return s;
+}
+
+GridView view_of(const pd_grid* g) {
+    GridView v;
+    v.pos = g->pos;
+    v.code = g->code;
+    v.leaf = g->leaf;
+    v.hash = g->hash;
+    v.hmask = g->hmask;
+    v.B = g->B;
+    v.shift = g->shift;
+    v.T = g->T;
+    v.origin = g->origin;
+    v.umax = g->umax;
+    return v;
+}
+
+#define CK(x)                                                                  \
+    do {                                                                       \
+        cudaError_t e_ = (x);                                                  \
+        if (e_ != cudaSuccess) {                                               \
+            if (e_ == cudaErrorMemoryAllocation) {                             \
+                set_err(g->ctx, "out of device memory at %s (line %lld)", #x,  \
+                        (long long)__LINE__);                                  \
+                return PD_ENOMEM;                                              \
+            }                                                                  \
+            set_err(g->ctx, "CUDA error at %s: %lld", #x, (long long)e_);      \
+            return PD_ECUDA;                                                   \
+        }                                                                      \
+    } while (0)
+
+#define ALLOC(ptr, type, count)                                                \
+    do {                                                                       \
+        ptr = (type*)ctx_alloc(g->ctx, sizeof(type) * (size_t)(count), g->st); \
+        if (!ptr) {                                                            \
+            set_err(g->ctx, "allocation of %s failed (%lld bytes)", #ptr,      \
+                    (long long)(sizeof(type) * (size_t)(count)));              \
+            return PD_ENOMEM;                                                  \
+        }                                                                      \
+    } while (0)
+
+void gfree(pd_grid* g, void* p) { ctx_free(g->ctx, p, g->st); }
+
+// S = stored neighbours per point for a cost with k neighbours
+int width_for(int k, int density_k1) {
+    if (density_k1) return 8;
+    if (k + 1 <= 4) return 4;
+    if (k + 1 <= 8) return 8;
+    return 17;
+}
+int filt_width(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 17); }
+
+// Octree leaf levels, cell hash and full-mode groups over pos/code[0, ng).
+int build_cells(pd_grid* g) {
+    Scratch s = scratch_of(g);
+    CK(launch_leaf_levels(g->code, g->ng, g->T, g->B, g->leaf, g->st));
+    CK(launch_node_count(g->code, g->leaf, g->ng, g->B, g->d_u64, g->st));
+    unsigned long long nodes = 0;
+    CK(cudaMemcpyAsync(&nodes, g->d_u64, sizeof(nodes), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    u64 cap = 1024;
+    while (cap < 2 * nodes) cap <<= 1;
+    if (g->hash && g->hmask + 1 < cap) {
+        gfree(g, g->hash);
+        g->hash = nullptr;
+    }
+    if (!g->hash) {
+        ALLOC(g->hash, HashSlot, cap);
+        g->hmask = cap - 1;
+    }
+    CK(launch_node_insert(g->code, g->leaf, g->ng, g->B, g->hash, g->hmask, g->st));
+    GridView v = view_of(g);
+    CK(launch_leaf_groups(v, g->ng, g->groups, g->d_int, g->st));
+    int ng = 0;
+    CK(cudaMemcpyAsync(&ng, g->d_int, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    g->ngroups = ng;
+    (void)s;
+    return PD_OK;
+}
+
+}  // namespace
+
+// ============================================================ API: context
+extern "C" int pd_ctx_create(const pd_allocator* alloc, pd_ctx** out) {
+    if (!out) return PD_EINVAL;
+    pd_ctx* c = (pd_ctx*)calloc(1, sizeof(pd_ctx));
+    if (!c) return PD_ENOMEM;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = 1;
+    }
+    *out = c;
+    return PD_OK;
+}
+
+extern "C" void pd_ctx_destroy(pd_ctx* ctx) { free(ctx); }
+
+extern "C" const char* pd_strerror(int code) {
+    switch (code) {
+        case PD_OK: return "ok";
+        case PD_EINVAL: return "invalid argument";
+        case PD_ERANGE: return "coordinate spread too large (>= 2^25 mm)";
+        case PD_ENOMEM: return "out of device memory";
+        case PD_ECUDA: return "CUDA runtime error";
+        case PD_ETIMEOUT: return "device wait timed out";
+        case PD_EINTERNAL: return "internal error";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+// ============================================================ API: grid
+static int grid_release(pd_grid* g) {
+    void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
+                    g->prim, g->nbr, g->rk2, g->flg, g->d_int, g->d_u64};
+    for (void* p : ptrs) gfree(g, p);
+    return PD_OK;
+}
+
+extern "C" int pd_grid_free(pd_grid* g) {
+    if (!g) return PD_EINVAL;
+    grid_release(g);
+    cudaStreamSynchronize(g->st);
+    delete g;
+    return PD_OK;
+}
+
+extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t* rgb_dev,
+                             int64_t n, const pd_grid_params* params, void* stream,
+                             pd_grid** out) {
+    if (!ctx || !out || !xyz_dev || n < 1 || n >= (1ll << 31) - 64) {
+        if (ctx) set_err(ctx, "pd_build_grid: invalid argument%s (n = %lld)", "", (long long)n);
+        return PD_EINVAL;
+    }
+    int T = params && params->leaf_max ? params->leaf_max : 32;
+    if (T < 4 || T > 32) {
+        set_err(ctx, "pd_build_grid: leaf_max must be in [4, 32]%s (got %lld)", "", T);
+        return PD_EINVAL;
+    }
+    pd_grid* g = new pd_grid();
+    memset(&g->stats, 0, sizeof(g->stats));
+    g->ctx = ctx;
+    g->st = (cudaStream_t)stream;
+    g->trace = getenv("PD_TRACE") != nullptr;
+    g->n = n;
+    g->ng = n;
+    g->T = T;
+    int rc = PD_OK;
+    auto fail = [&](int code) {
+        grid_release(g);
+        delete g;
+        return code;
+    };
+#define TRY(x)                  \
+    do {                        \
+        rc = (x);               \
+        if (rc) return fail(rc); \
+    } while (0)
+    auto body = [&]() -> int {
+        ALLOC(g->d_int, int, 8);
+        ALLOC(g->d_u64, unsigned long long, 4);
+        int* d6 = (int*)g->d_int;
+        CK(launch_bbox(xyz_dev, n, d6, g->st));
+        int h6[6];
+        CK(cudaMemcpyAsync(h6, d6, sizeof(h6), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        long long span = 0;
+        for (int a = 0; a < 3; a++) span = std::max(span, (long long)h6[3 + a] - h6[a]);
+        if (span >= (1ll << 25)) {
+            set_err(ctx, "pd_build_grid: coordinate spread %s%lld mm >= 2^25", "", span);
+            return PD_ERANGE;
+        }
+        g->origin = make_int3(h6[0], h6[1], h6[2]);
+        g->umax = make_int3(h6[3] - h6[0], h6[4] - h6[1], h6[5] - h6[2]);
+        int bits = 1;
+        while ((1ll << bits) <= span) bits++;
+        g->shift = bits > PD_MAXLEVEL ? bits - PD_MAXLEVEL : 0;
+        g->B = bits - g->shift;
+        if (g->B < 1) g->B = 1;
+        ALLOC(g->code, u64, n);
+        uint32_t* perm;
+        ALLOC(perm, uint32_t, n);
+        Scratch s = scratch_of(g);
+        CK(launch_morton(xyz_dev, n, g->origin, g->shift, g->code, perm, g->st));
+        CK(radix_sort_pairs(g->code, perm, n, 3 * g->B, s, g->st));
+        ALLOC(g->pos, int4, n);
+        if (rgb_dev) ALLOC(g->rgb, uchar4, n);
+        CK(launch_gather(xyz_dev, rgb_dev, nullptr, perm, n, g->pos, g->rgb, nullptr, g->st));
+        gfree(g, perm);
+        ALLOC(g->leaf, uint8_t, n);
+        ALLOC(g->alive, uint8_t, n);
+        CK(cudaMemsetAsync(g->alive, 1, n, g->st));
+        ALLOC(g->groups, int4, n);
+        return build_cells(g);
+    };
+    TRY(body());
+#undef TRY
+    *out = g;
+    return PD_OK;
+}
+
+extern "C" int pd_grid_stats(const pd_grid* g, pd_stats* out) {
+    if (!g || !out) return PD_EINVAL;
+    *out = g->stats;
+    return PD_OK;
+}
+
+// ============================================================ neighbour state
+namespace {
+
+int check_cost(pd_grid* g, const pd_cost_params* cp) {
+    if (!cp || cp->k < 1 || cp->k > PD_KMAX || cp->term < 0 || cp->term > 2) {
+        set_err(g->ctx, "invalid cost parameters%s (k = %lld)", "", cp ? cp->k : -1);
+        return PD_EINVAL;
+    }
+    if (cp->term == PD_TERM_COLOR && !g->rgb) {
+        set_err(g->ctx, "colour term needs rgb at pd_build_grid%s", "", 0);
+        return PD_EINVAL;
+    }
+    if (cp->term == PD_TERM_ORIENT && !cp->normals_dev) {
+        set_err(g->ctx, "orientation term needs normals_dev%s", "", 0);
+        return PD_EINVAL;
+    }
+    return PD_OK;
+}
+
+// (Re)allocate the neighbour state for a cost and gather normals.
+int prepare_state(pd_grid* g, const pd_cost_params* cp) {
+    int dk1 = cp->k == 1 && cp->term == PD_TERM_NONE;
+    int S = width_for(cp->k, dk1);
+    if (g->nbr && g->S != S) {
+        gfree(g, g->nbr);
+        g->nbr = nullptr;
+    }
+    g->S = S;
+    g->k = cp->k;
+    g->density_k1 = dk1;
+    if (!g->prim) ALLOC(g->prim, u64, g->n);
+    if (!g->nbr) ALLOC(g->nbr, int, (size_t)g->n * S);
+    if (!g->rk2) ALLOC(g->rk2, u64, g->n);
+    if (!g->flg) ALLOC(g->flg, uint8_t, g->n);
+    if (cp->term == PD_TERM_ORIENT) {
+        if (!g->nrm) ALLOC(g->nrm, float4, g->n);
+        // normals are given in input order: gather through pos[].w
+        CK(launch_gather_nrm(cp->normals_dev, g->pos, g->ng, g->nrm, g->st));
+    }
+    return PD_OK;
+}
+
+KnnArgs base_args(pd_grid* g, const pd_cost_params* cp) {
+    KnnArgs a;
+    memset(&a, 0, sizeof(a));
+    a.groups = g->groups;
+    a.ngroups = g->ngroups;
+    a.alive = g->alive;
+    a.prim = g->prim;
+    a.k = cp->k;
+    a.S = g->S;
+    a.density_k1 = g->density_k1;
+    a.term = cp->term;
+    a.weight = cp->weight;
+    a.rgb = g->rgb;
+    a.nrm = g->nrm;
+    a.nbr = g->nbr;
+    a.prim_out = g->prim;
+    a.rk2_out = g->rk2;
+    a.flg_out = g->flg;
+    return a;
+}
+
+// Deferred event timing: pairs of events recorded on the launching stream,
+// resolved once at the end of a call (no synchronisation per launch).
+struct Timers {
+    struct Span {
+        cudaEvent_t a, b;
+        double* acc;
+    };
+    std::vector<Span> spans;
+    cudaStream_t st;
+    explicit Timers(cudaStream_t s) : st(s) {}
+    Span* open(double* acc) {
+        Span sp;
+        cudaEventCreate(&sp.a);
+        cudaEventCreate(&sp.b);
+        sp.acc = acc;
+        cudaEventRecord(sp.a, st);
+        spans.push_back(sp);
+        return &spans.back();
+    }
+    void close() { cudaEventRecord(spans.back().b, st); }
+    void resolve() {
+        for (auto& sp : spans) {
+            cudaEventSynchronize(sp.b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, sp.a, sp.b);
+            *sp.acc += ms;
+            cudaEventDestroy(sp.a);
+            cudaEventDestroy(sp.b);
+        }
+        spans.clear();
+    }
+    ~Timers() { resolve(); }
+};
+struct Span {
+    Timers& t;
+    Span(Timers& tt, double* acc) : t(tt) { t.open(acc); }
+    ~Span() { t.close(); }
+};
+
+// kNN over every grid point (full mode)
+int knn_all(pd_grid* g, const pd_cost_params* cp, double* cost_s) {
+    KnnArgs a = base_args(g, cp);
+    a.cost_out = cost_s;
+    CK(launch_knn(view_of(g), a, g->st));
+    return PD_OK;
+}
+
+// kNN over an ordered list of Morton positions (len on host)
+int knn_list(pd_grid* g, const pd_cost_params* cp, const int* list, int len, int filter,
+             int S, u64 tp, int ti, u64* fout) {
+    if (len <= 0) return PD_OK;
+    Scratch s = scratch_of(g);
+    int4* groups;
+    ALLOC(groups, int4, len);
+    int* d_ng = g->d_int + 1;
+    CK(launch_list_groups(view_of(g), list, len, groups, d_ng, s, g->st));
+    int ngr = 0;
+    CK(cudaMemcpyAsync(&ngr, d_ng, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    KnnArgs a = base_args(g, cp);
+    a.groups = groups;
+    a.ngroups = ngr;
+    a.list = list;
+    a.filter = filter;
+    a.S = S;
+    a.tau_prim = tp;
+    a.tau_idx = ti;
+    if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
+    if (filter == FILT_BELOW_TAU) a.lam_out = fout;
+    CK(launch_knn(view_of(g), a, g->st));
+    gfree(g, groups);
+    return PD_OK;
+}
+
+// Compact the live points into a fresh grid order (keeps Morton order) and
+// rebuild the cell table; stored neighbours are remapped (A7).
+int compact_rebuild(pd_grid* g, bool remap_state) {
+    Scratch s = scratch_of(g);
+    int* list;
+    ALLOC(list, int, g->ng);
+    int* d_cnt = g->d_int + 2;
+    CK(stable_compact(g->alive, g->ng, list, d_cnt, s, g->st));
+    int nl = 0;
+    CK(cudaMemcpyAsync(&nl, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    int* newpos;
+    ALLOC(newpos, int, g->ng);
+    CK(cudaMemsetAsync(newpos, 0xff, g->ng * sizeof(int), g->st));  // -1: not kept
+    CK(launch_newpos(list, nl, newpos, g->st));
+    int4* pos2;
+    ALLOC(pos2, int4, g->n);
+    CK(launch_take_i4(list, nl, g->pos, pos2, g->st));
+    gfree(g, g->pos);
+    g->pos = pos2;
+    u64* code2;
+    ALLOC(code2, u64, g->n);
+    CK(launch_take_u64(list, nl, g->code, code2, g->st));
+    gfree(g, g->code);
+    g->code = code2;
+    if (g->rgb) {
+        uchar4* r2;
+        ALLOC(r2, uchar4, g->n);
+        CK(launch_take_uc4(list, nl, g->rgb, r2, g->st));
+        gfree(g, g->rgb);
+        g->rgb = r2;
+    }
+    if (g->nrm) {
+        float4* n2;
+        ALLOC(n2, float4, g->n);
+        CK(launch_take_f4(list, nl, g->nrm, n2, g->st));
+        gfree(g, g->nrm);
+        g->nrm = n2;
+    }
+    if (remap_state) {
+        u64* p2;
+        ALLOC(p2, u64, g->n);
+        CK(launch_take_u64(list, nl, g->prim, p2, g->st));
+        gfree(g, g->prim);
+        g->prim = p2;
+        u64* r2;
+        ALLOC(r2, u64, g->n);
+        CK(launch_take_u64(list, nl, g->rk2, r2, g->st));
+        gfree(g, g->rk2);
+        g->rk2 = r2;
+        uint8_t* f2;
+        ALLOC(f2, uint8_t, g->n);
+        CK(launch_take_u8(list, nl, g->flg, f2, g->st));
+        gfree(g, g->flg);
+        g->flg = f2;
+        int* nb2;
+        ALLOC(nb2, int, (size_t)g->n * g->S);
+        CK(launch_remap(list, nl, g->nbr, nb2, newpos, g->ng, g->S, g->st));
+        gfree(g, g->nbr);
+        g->nbr = nb2;
+    }
+    gfree(g, newpos);
+    gfree(g, list);
+    g->ng = nl;
+    CK(cudaMemsetAsync(g->alive, 1, nl, g->st));
+    g->stats.grid_builds++;
+    return build_cells(g);
+}
+
+// r-th largest live key (1-based).  With band_rank > 0 also returns the
+// lower boundary of the first-digit bin holding the band_rank-th largest key.
+struct Sel {
+    u64 prim;
+    int idx;
+};
+
+Sel key_from_digits(const uint32_t* d, int npass) {
+    // 96-bit value with digits 0..npass-1 set and the rest zero
+    unsigned __int128 v = 0;
+    for (int p = 0; p < 8; p++) {
+        v <<= 12;
+        if (p < npass) v |= d[p];
+    }
+    Sel s;
+    s.prim = (u64)(v >> 32);
+    s.idx = (int)(uint32_t)v;
+    return s;
+}
+
+int select_rank(pd_grid* g, const u64* prim, const uint8_t* alive, int64_t r, int64_t band_rank,
+                Sel* out, Sel* band_out) {
+    uint32_t* hist;
+    ALLOC(hist, uint32_t, 4096);
+    std::vector<uint32_t> h(4096);
+    uint32_t pre[8] = {0};
+    u64* bufA = nullptr;
+    int* idA = nullptr;
+    int64_t len = 0;
+    int* d_cnt = g->d_int + 3;
+    int rc = PD_OK;
+    bool done = false;
+    for (int pass = 0; pass < 8 && !done; pass++) {
+        CK(launch_sel_hist(prim, alive, g->ng, pass ? bufA : nullptr, idA, len, pass, pre, hist,
+                           g->st));
+        CK(cudaMemcpyAsync(h.data(), hist, 4096 * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           g->st));
+        CK(cudaStreamSynchronize(g->st));
+        int64_t cum = 0;
+        int b = 4095;
+        for (; b >= 0; b--) {
+            if (cum + h[b] >= r) break;
+            cum += h[b];
+        }
+        if (b < 0) {
+            set_err(g->ctx, "select_rank: rank beyond live count%s (r = %lld)", "", r);
+            rc = PD_EINTERNAL;
+            break;
+        }
+        if (pass == 0 && band_out) {
+            int64_t c2 = 0;
+            int bb = 4095;
+            for (; bb > 0; bb--) {
+                if (c2 + h[bb] >= band_rank) break;
+                c2 += h[bb];
+            }
+            uint32_t d0[8] = {(uint32_t)bb};
+            *band_out = key_from_digits(d0, 1);
+        }
+        pre[pass] = (uint32_t)b;
+        if (cum + h[b] == r || pass == 7) {
+            *out = key_from_digits(pre, pass + 1);
+            done = true;
+            break;
+        }
+        r -= cum;
+        int64_t nlen = h[b];
+        u64* nb;
+        int* ni;
+        ALLOC(nb, u64, nlen);
+        ALLOC(ni, int, nlen);
+        CK(launch_sel_compact(prim, g->pos, alive, g->ng, pass ? bufA : nullptr, idA, len, pass,
+                              pre, nb, ni, d_cnt, g->st));
+        if (bufA) {
+            gfree(g, bufA);
+            gfree(g, idA);
+        }
+        bufA = nb;
+        idA = ni;
+        len = nlen;
+    }
+    if (bufA) {
+        gfree(g, bufA);
+        gfree(g, idA);
+    }
+    gfree(g, hist);
+    return rc;
+}
+
+bool sel_gt(const Sel& a, const Sel& b) {
+    return a.prim > b.prim || (a.prim == b.prim && a.idx > b.idx);
+}
+
+// Duplicate phase: coincident points beyond the smallest index of their
+// class are the first pops of the sequential greedy (their cost is +inf).
+int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
+    *removed = 0;
+    uint8_t* dup;
+    ALLOC(dup, uint8_t, g->ng);
+    CK(launch_dup_flag(g->code, g->pos, g->ng, dup, g->d_u64, g->st));
+    unsigned long long nd = 0;
+    CK(cudaMemcpyAsync(&nd, g->d_u64, sizeof(nd), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    int idx_min = 0;
+    if (nd > 0 && need > 0) {
+        if ((int64_t)nd > need) {
+            // the need largest input indices among the duplicates
+            u64* zeros;
+            ALLOC(zeros, u64, g->ng);
+            CK(cudaMemsetAsync(zeros, 0, g->ng * sizeof(u64), g->st));
+            Sel s;
+            int rc = select_rank(g, zeros, dup, need, 0, &s, nullptr);
+            gfree(g, zeros);
+            if (rc) return rc;
+            idx_min = s.idx;
+            *removed = need;
+        } else {
+            *removed = (int64_t)nd;
+        }
+        CK(launch_dup_remove(dup, g->pos, g->ng, idx_min, g->alive, g->st));
+    }
+    gfree(g, dup);
+    return PD_OK;
+}
+
+int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev) {
+    int rc = check_cost(g, cp);
+    if (rc) return rc;
+    if (m < 0 || m > g->n || !keep_dev) {
+        set_err(g->ctx, "pd_decimate: m must be in [0, n] and keep_dev set%s (m = %lld)", "", m);
+        return PD_EINVAL;
+    }
+    if (g->ng != g->n) {
+        set_err(g->ctx, "pd_decimate: grid already decimated; build a new one%s", "", 0);
+        return PD_EINVAL;
+    }
+    memset(&g->stats, 0, sizeof(g->stats));
+    g->stats.n = g->n;
+    g->stats.m = m;
+    long long launches0 = g_launch_count;
+    Timers T(g->st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, g->st);
+    rc = prepare_state(g, cp);
+    if (rc) return rc;
+    int k = cp->k;
+    double band = cp->band > 0 ? cp->band : 0.2;
+    int64_t live = g->n;
+    // ---- duplicate phase
+    int64_t nd = 0;
+    rc = remove_duplicates(g, live - m, &nd);
+    if (rc) return rc;
+    g->stats.dup_removed = nd;
+    live -= nd;
+    if (nd > 0) {
+        rc = compact_rebuild(g, false);
+        if (rc) return rc;
+    }
+    // ---- first neighbour pass
+    {
+        Span t(T, &g->stats.ms_knn_first);
+        rc = knn_all(g, cp, nullptr);
+        if (rc) return rc;
+    }
+    g->stats.q_first = g->ng;
+    int S = g->S;
+    int Sf = filt_width(k);
+    uint8_t *inP, *rej, *dirty, *fqf, *dgf;
+    int *cand, *slow, *list, *fql, *dgl;
+    u64 *fprim, *lam;
+    int2* pairs;
+    int64_t cap = g->n;
+    ALLOC(inP, uint8_t, cap);
+    ALLOC(rej, uint8_t, cap);
+    ALLOC(dirty, uint8_t, cap);
+    ALLOC(cand, int, cap);
+    ALLOC(slow, int, cap);
+    ALLOC(list, int, cap);
+    CK(cudaMemsetAsync(inP, 0, cap, g->st));
+    CK(cudaMemsetAsync(rej, 0, cap, g->st));
+    int pair_cap = 0;
+    fqf = dgf = nullptr;
+    fql = dgl = nullptr;
+    fprim = lam = nullptr;
+    pairs = nullptr;
+    if (!g->density_k1) {
+        ALLOC(fqf, uint8_t, cap);
+        ALLOC(dgf, uint8_t, cap);
+        ALLOC(fql, int, cap);
+        ALLOC(dgl, int, cap);
+        ALLOC(fprim, u64, cap);
+        ALLOC(lam, u64, cap);
+        pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
+        ALLOC(pairs, int2, pair_cap);
+    }
+    int* d = g->d_int;  // [4] ncand [5] nslow [6] changed [7] misc
+    Scratch s = scratch_of(g);
+    int64_t built = live;
+    while (live > m) {
+        int64_t need = live - m;
+        g->stats.rounds++;
+        if (g->stats.rounds > 1000000) {
+            set_err(g->ctx, "pd_decimate: round limit reached%s (live = %lld)", "", live);
+            return PD_EINTERNAL;
+        }
+        Sel kst, bnd;
+        int64_t band_rank = std::max<int64_t>(1, (int64_t)(band * (double)live));
+        rc = select_rank(g, g->prim, g->alive, need, 0, &kst, nullptr);
+        if (rc) return rc;
+        Sel tau = kst;
+        if (!g->density_k1 && band_rank < need) {
+            // k >= 2: examine only the band_rank largest keys this round
+            rc = select_rank(g, g->prim, g->alive, band_rank, 0, &bnd, nullptr);
+            if (rc) return rc;
+            if (sel_gt(bnd, tau)) tau = bnd;
+        }
+        CK(cudaMemsetAsync(d + 4, 0, 4 * sizeof(int), g->st));
+        int hc[4];
+        if (g->density_k1) {
+            CK(launch_k1_cand(g->prim, g->pos, g->alive, g->nbr, g->flg, g->ng, S, tau.prim,
+                              tau.idx, inP, cand, d + 4, slow, d + 5, g->st));
+            CK(cudaMemcpyAsync(hc, d + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+            CK(cudaStreamSynchronize(g->st));
+            if (hc[1] > 0)
+                CK(launch_k1_slow(view_of(g), g->prim, g->alive, g->rk2, slow, d + 5, hc[1], inP,
+                                  cand, d + 4, g->st));
+            CK(cudaMemcpyAsync(hc, d + 4, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+            CK(cudaStreamSynchronize(g->st));
+            int ncand = hc[0];
+            for (int it = 0; it < 100000; it++) {
+                CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
+                CK(launch_k1_fix(cand, d + 4, ncand, g->pos, g->nbr, S, inP, rej, d + 6, g->st));
+                int ch = 0;
+                CK(cudaMemcpyAsync(&ch, d + 6, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+                CK(cudaStreamSynchronize(g->st));
+                if (!ch) break;
+            }
+            CK(launch_remove(cand, d + 4, ncand, inP, rej, g->alive, g->d_u64, g->st));
+        } else {
+            for (int attempt = 0; attempt < 2; attempt++) {
+                if (attempt == 1) {
+                    // only the global maximum: always removable
+                    Sel top;
+                    rc = select_rank(g, g->prim, g->alive, 1, 0, &top, nullptr);
+                    if (rc) return rc;
+                    tau = top;
+                    CK(cudaMemsetAsync(d + 4, 0, 4 * sizeof(int), g->st));
+                }
+                if (attempt == 1) {
+                    CK(launch_accept_above(g->prim, g->pos, g->alive, g->ng, tau.prim, tau.idx,
+                                           inP, cand, d + 4, g->st));
+                    break;
+                }
+                CK(launch_kk_cand(g->prim, g->pos, g->alive, g->nbr, g->flg, g->ng, S, k,
+                                  tau.prim, tau.idx, inP, cand, d + 4, fqf, dgf, g->st));
+                // (A) by a search restricted to smaller keys
+                CK(stable_compact(fqf, g->ng, fql, d + 7, s, g->st));
+                int nfq = 0, ndg = 0;
+                CK(cudaMemcpyAsync(&nfq, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+                CK(cudaStreamSynchronize(g->st));
+                g->stats.filtered_queries += nfq;
+                {
+                    Span t(T, &g->stats.ms_knn);
+                    rc = knn_list(g, cp, fql, nfq, FILT_BELOW_SELF, Sf, 0, 0, fprim);
+                    if (rc) return rc;
+                }
+                CK(cudaMemcpyAsync(d + 7, &nfq, sizeof(int), cudaMemcpyHostToDevice, g->st));
+                CK(launch_kk_accept(fql, d + 7, nfq, g->prim, fprim, inP, cand, d + 4, g->st));
+                // (B) danger pairs from points above tau with band points nearby
+                CK(stable_compact(dgf, g->ng, dgl, d + 7, s, g->st));
+                CK(cudaMemcpyAsync(&ndg, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+                CK(cudaStreamSynchronize(g->st));
+                g->stats.danger_queries += ndg;
+                {
+                    Span t(T, &g->stats.ms_knn);
+                    rc = knn_list(g, cp, dgl, ndg, FILT_BELOW_TAU, Sf, tau.prim, tau.idx, lam);
+                    if (rc) return rc;
+                }
+                CK(cudaMemcpyAsync(d + 7, &ndg, sizeof(int), cudaMemcpyHostToDevice, g->st));
+                CK(cudaMemsetAsync(d + 5, 0, 2 * sizeof(int), g->st));  // npairs, overflow
+                CK(launch_danger(view_of(g), dgl, d + 7, ndg, g->prim, g->alive, inP, rej, lam,
+                                 k, pairs, d + 5, pair_cap, d + 6, g->st));
+                CK(cudaMemcpyAsync(hc, d + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
+                CK(cudaStreamSynchronize(g->st));
+                if (hc[2]) {
+                    // pair overflow or too few low points: clear and take the global max only
+                    CK(launch_remove(cand, d + 4, 0, inP, rej, g->alive, g->d_u64, g->st));
+                    // clear inP for all current candidates
+                    CK(cudaMemsetAsync(inP, 0, cap, g->st));
+                    CK(cudaMemsetAsync(rej, 0, cap, g->st));
+                    continue;
+                }
+                int npairs = std::min(hc[1], pair_cap);
+                for (int it = 0; it < 100000 && npairs > 0; it++) {
+                    CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
+                    CK(launch_pair_fix(pairs, d + 5, npairs, pair_cap, inP, rej, d + 6, g->st));
+                    int ch = 0;
+                    CK(cudaMemcpyAsync(&ch, d + 6, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+                    CK(cudaStreamSynchronize(g->st));
+                    if (!ch) break;
+                }
+                break;
+            }
+            int ncand = 0;
+            CK(cudaMemcpyAsync(&ncand, d + 4, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+            CK(cudaStreamSynchronize(g->st));
+            CK(launch_remove(cand, d + 4, ncand, inP, rej, g->alive, g->d_u64, g->st));
+        }
+        unsigned long long removed = 0;
+        CK(cudaMemcpyAsync(&removed, g->d_u64, sizeof(removed), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        if (removed == 0 || (int64_t)removed > need) {
+            int dbg[4] = {0, 0, 0, 0};
+            cudaMemcpy(dbg, d + 4, sizeof(dbg), cudaMemcpyDeviceToHost);
+            snprintf(g->ctx->err, sizeof(g->ctx->err),
+                     "pd_decimate: round %d removed %llu points (need %lld, live %lld, "
+                     "candidates %d, slow %d, tau %016llx:%d)",
+                     g->stats.rounds, removed, (long long)need, (long long)live, dbg[0], dbg[1],
+                     (unsigned long long)tau.prim, tau.idx);
+            return PD_EINTERNAL;
+        }
+        if (g->trace) {
+            int dbg[4] = {0, 0, 0, 0};
+            cudaMemcpy(dbg, d + 4, sizeof(dbg), cudaMemcpyDeviceToHost);
+            fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu\n",
+                    g->stats.rounds, (long long)live, (long long)need, dbg[0], removed);
+        }
+        live -= (int64_t)removed;
+        if (live <= m) break;
+        // re-search the points whose stored neighbours were removed
+        CK(launch_dirty(g->alive, g->nbr, g->ng, S, g->density_k1 ? S : k, dirty, g->st));
+        CK(stable_compact(dirty, g->ng, list, d + 7, s, g->st));
+        int nl = 0;
+        CK(cudaMemcpyAsync(&nl, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        g->stats.requeries += nl;
+        {
+            Span t(T, &g->stats.ms_knn_requery);
+            rc = knn_list(g, cp, list, nl, FILT_NONE, S, 0, 0, nullptr);
+            if (rc) return rc;
+        }
+        // every live point now stores live neighbours only: safe to compact
+        if (live * 2 < built) {
+            Span t(T, &g->stats.ms_build);
+            rc = compact_rebuild(g, true);
+            if (rc) return rc;
+            built = live;
+        }
+    }
+    CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
+    CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
+    void* fr[] = {inP, rej, dirty, cand, slow, list, fqf, dgf, fql, dgl, fprim, lam, pairs};
+    for (void* p : fr) gfree(g, p);
+    cudaEventRecord(e1, g->st);
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    g->stats.ms_total = ms;
+    T.resolve();
+    g->stats.ms_knn += g->stats.ms_knn_first + g->stats.ms_knn_requery;
+    g->stats.ms_rules = ms - g->stats.ms_knn - g->stats.ms_build;
+    g->stats.launches = g_launch_count - launches0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->ng = 0;  // consumed
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" int pd_knn_cost(pd_grid* g, const pd_cost_params* cp, double* cost_dev,
+                           int32_t* knn_dev, void* stream) {
+    if (!g) return PD_EINVAL;
+    g->st = (cudaStream_t)stream;
+    int rc = check_cost(g, cp);
+    if (rc) return rc;
+    if (g->ng != g->n) {
+        set_err(g->ctx, "pd_knn_cost: grid already decimated%s", "", 0);
+        return PD_EINVAL;
+    }
+    rc = prepare_state(g, cp);
+    if (rc) return rc;
+    double* cost_s;
+    ALLOC(cost_s, double, g->n);
+    rc = knn_all(g, cp, cost_s);
+    if (rc) return rc;
+    CK(launch_knn_out(g->pos, cost_s, g->nbr, g->ng, g->S, cp->k, cost_dev, knn_dev, g->st));
+    gfree(g, cost_s);
+    CK(cudaStreamSynchronize(g->st));
+    return PD_OK;
+}
+
+extern "C" int pd_decimate_count(pd_grid* g, const pd_cost_params* cp, int64_t m,
+                                 uint8_t* keep_dev, void* stream) {
+    if (!g) return PD_EINVAL;
+    g->st = (cudaStream_t)stream;
+    int rc = decimate_impl(g, cp, m, keep_dev);
+    cudaError_t e = cudaStreamSynchronize(g->st);
+    if (!rc && e) {
+        set_err(g->ctx, "pd_decimate: CUDA error %s%lld", "", (long long)e);
+        rc = PD_ECUDA;
+    }
+    return rc;
+}
+
+extern "C" int pd_decimate_ratio(pd_grid* g, const pd_cost_params* cp, double ratio,
+                                 uint8_t* keep_dev, void* stream) {
+    if (!g || !(ratio >= 0.0 && ratio <= 1.0)) {
+        if (g) set_err(g->ctx, "pd_decimate_ratio: ratio must be in [0, 1]%s", "", 0);
+        return PD_EINVAL;
+    }
+    double v = ratio * (double)g->n;
+    int64_t m = (int64_t)v;  // floor for non-negative values
+    return pd_decimate_count(g, cp, m, keep_dev, stream);
+}
+
+extern "C" int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_host,
+                                const float* normals_host, int64_t n, const pd_cost_params* cp,
+                                int64_t m, uint8_t* keep_host, void* stream, pd_stats* stats) {
+    if (!ctx || !xyz_host || !keep_host || !cp || n < 1) return PD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t* xyz = (int32_t*)ctx_alloc(ctx, (size_t)n * 12, st);
+    uint8_t* rgb = rgb_host ? (uint8_t*)ctx_alloc(ctx, (size_t)n * 3, st) : nullptr;
+    float* nrm = normals_host && cp->term == PD_TERM_ORIENT
+                     ? (float*)ctx_alloc(ctx, (size_t)n * 12, st)
+                     : nullptr;
+    uint8_t* keep = (uint8_t*)ctx_alloc(ctx, (size_t)n, st);
+    int rc = PD_OK;
+    if (!xyz || !keep || (rgb_host && !rgb) || (normals_host && cp->term == PD_TERM_ORIENT && !nrm)) {
+        set_err(ctx, "pd_decimate_host: allocation failed%s", "", 0);
+        rc = PD_ENOMEM;
+    }
+    pd_grid* g = nullptr;
+    if (!rc && cudaMemcpyAsync(xyz, xyz_host, (size_t)n * 12, cudaMemcpyHostToDevice, st))
+        rc = PD_ECUDA;
+    if (!rc && rgb && cudaMemcpyAsync(rgb, rgb_host, (size_t)n * 3, cudaMemcpyHostToDevice, st))
+        rc = PD_ECUDA;
+    if (!rc && nrm && cudaMemcpyAsync(nrm, normals_host, (size_t)n * 12, cudaMemcpyHostToDevice, st))
+        rc = PD_ECUDA;
+    if (!rc) rc = pd_build_grid(ctx, xyz, rgb, n, nullptr, stream, &g);
+    if (!rc) {
+        pd_cost_params c2 = *cp;
+        if (nrm) c2.normals_dev = nrm;
+        rc = pd_decimate_count(g, &c2, m, keep, stream);
+        if (!rc && stats) pd_grid_stats(g, stats);
+    }
+    if (!rc && cudaMemcpyAsync(keep_host, keep, (size_t)n, cudaMemcpyDeviceToHost, st))
+        rc = PD_ECUDA;
+    if (g) pd_grid_free(g);
+    ctx_free(ctx, xyz, st);
+    ctx_free(ctx, rgb, st);
+    ctx_free(ctx, nrm, st);
+    ctx_free(ctx, keep, st);
+    if (cudaStreamSynchronize(st) && !rc) rc = PD_ECUDA;
+    return rc;
+}
+
+// Internal diagnostics (not part of pd.h): copy one state array of the grid
+// (in Morton order) to host memory.  what: 0 pos int4, 1 code u64, 2 leaf u8,
+// 3 alive u8, 4 prim u64, 5 nbr int32 (S per point), 6 flg u8, 7 groups int4,
+// 8 scalars int64[8] = {n, ng, ngroups, B, shift, S, hmask+1, T}.
+extern "C" int pd__debug_dump(pd_grid* g, int what, void* host, int64_t bytes) {
+    if (!g || !host) return PD_EINVAL;
+    const void* src = nullptr;
+    size_t sz = 0;
+    switch (what) {
+        case 0: src = g->pos; sz = sizeof(int4) * g->ng; break;
+        case 1: src = g->code; sz = sizeof(u64) * g->ng; break;
+        case 2: src = g->leaf; sz = g->ng; break;
+        case 3: src = g->alive; sz = g->ng; break;
+        case 4: src = g->prim; sz = sizeof(u64) * g->ng; break;
+        case 5: src = g->nbr; sz = sizeof(int) * g->ng * g->S; break;
+        case 6: src = g->flg; sz = g->ng; break;
+        case 7: src = g->groups; sz = sizeof(int4) * g->ngroups; break;
+        case 8: {
+            int64_t v[8] = {g->n, g->ng, g->ngroups, g->B, g->shift, g->S,
+                            (int64_t)(g->hmask + 1), g->T};
+            memcpy(host, v, std::min<int64_t>(bytes, sizeof(v)));
+            return PD_OK;
+        }
+        default: return PD_EINVAL;
+    }
+    if (!src) return PD_EINVAL;
+    if ((int64_t)sz > bytes) sz = (size_t)bytes;
+    cudaStreamSynchronize(g->st);
+    return cudaMemcpy(host, src, sz, cudaMemcpyDeviceToHost) ? PD_ECUDA : PD_OK;
+}
+
+// Internal diagnostics: run the duplicate phase and the first neighbour pass
+// of a decimation and stop (state left in the grid for pd__debug_dump).
+extern "C" int pd__debug_first_pass(pd_grid* g, const pd_cost_params* cp, int64_t m) {
+    if (!g) return PD_EINVAL;
+    int rc = check_cost(g, cp);
+    if (rc) return rc;
+    rc = prepare_state(g, cp);
+    if (rc) return rc;
+    int64_t nd = 0;
+    rc = remove_duplicates(g, g->n - m, &nd);
+    if (rc) return rc;
+    if (nd > 0) {
+        rc = compact_rebuild(g, false);
+        if (rc) return rc;
+    }
+    rc = knn_all(g, cp, nullptr);
+    cudaStreamSynchronize(g->st);
+    return rc;
+}
+
+// Internal: kernels launched by this library so far in the process.
+extern "C" long long pd__launch_count(void) { return g_launch_count; }

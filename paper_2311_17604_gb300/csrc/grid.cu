@@ -1,0 +1,504 @@
+// grid.cu -- voxel-grid build: extent, Morton codes, stable LSD radix sort,
+// gather into Morton order, adaptive octree leaf levels and the hashed table
+// of octree cells (the paper's voxelisation, section "Sub-sampling algorithm",
+// rebuilt as one sort that serves every power-of-two cell size).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+namespace pd {
+
+// ------------------------------------------------------------------ extent
+__global__ void bbox_kernel(const int32_t* __restrict__ xyz, int64_t n, int* out6) {
+    int mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            int v = xyz[3 * i + a];
+            mn[a] = min(mn[a], v);
+            mx[a] = max(mx[a], v);
+        }
+    }
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o; o >>= 1) {
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; a++) {
+            atomicMin(&out6[a], mn[a]);
+            atomicMax(&out6[3 + a], mx[a]);
+        }
+    }
+}
+
+cudaError_t launch_bbox(const int32_t* xyz, int64_t n, int* out6, cudaStream_t st) {
+    int init[6] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN};
+    cudaError_t e = cudaMemcpyAsync(out6, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e) return e;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    bbox_kernel<<<blocks, 256, 0, st>>>(xyz, n, out6); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Morton
+__global__ void morton_kernel(const int32_t* __restrict__ xyz, int64_t n, int3 o, int shift,
+                              u64* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t ux = (uint32_t)(xyz[3 * i] - o.x) >> shift;
+    uint32_t uy = (uint32_t)(xyz[3 * i + 1] - o.y) >> shift;
+    uint32_t uz = (uint32_t)(xyz[3 * i + 2] - o.z) >> shift;
+    keys[i] = morton3(ux, uy, uz);
+    vals[i] = (uint32_t)i;
+}
+
+cudaError_t launch_morton(const int32_t* xyz, int64_t n, int3 origin, int shift, u64* keys,
+                          uint32_t* vals, cudaStream_t st) {
+    morton_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xyz, n, origin, shift, keys, vals); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sum of uint32 (block = 256 threads x 4 items = 1024).
+__global__ void scan_block_kernel(uint32_t* data, int64_t len, uint32_t* sums) {
+    __shared__ uint32_t wsum[8];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int64_t base = (int64_t)blockIdx.x * 1024 + t * 4;
+    uint32_t v[4];
+    uint32_t acc = 0;
+    for (int j = 0; j < 4; j++) {
+        v[j] = base + j < len ? data[base + j] : 0;
+        acc += v[j];
+    }
+    uint32_t inc = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < 8 ? wsum[lane] : 0;
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < 8) wsum[lane] = s;
+    }
+    __syncthreads();
+    uint32_t off = (w ? wsum[w - 1] : 0) + inc - acc;
+    for (int j = 0; j < 4; j++) {
+        if (base + j < len) data[base + j] = off;
+        off += v[j];
+    }
+    if (t == 255 && sums) sums[blockIdx.x] = wsum[7];
+}
+
+__global__ void scan_add_kernel(uint32_t* data, int64_t len, const uint32_t* sums) {
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    uint32_t add = sums[blockIdx.x];
+    for (int j = 0; j < 4; j++, i += 256)
+        if (i < len) data[i] += add;
+}
+
+cudaError_t exclusive_scan_u32(uint32_t* data, int64_t len, const Scratch& s, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    int64_t nb = (len + 1023) / 1024;
+    if (nb == 1) {
+        scan_block_kernel<<<1, 256, 0, st>>>(data, len, nullptr); note_launch();
+        return cudaGetLastError();
+    }
+    uint32_t* sums = (uint32_t*)s.get(nb * sizeof(uint32_t));
+    if (!sums) return cudaErrorMemoryAllocation;
+    scan_block_kernel<<<(unsigned)nb, 256, 0, st>>>(data, len, sums); note_launch();
+    cudaError_t e = exclusive_scan_u32(sums, nb, s, st);
+    if (!e) scan_add_kernel<<<(unsigned)nb, 256, 0, st>>>(data, len, sums); note_launch();
+    s.put(sums);
+    return e ? e : cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ radix sort
+// Tiles of 2048 keys: 256 threads x 8 sub-tiles of 256 consecutive keys.
+#define RS_TILE 2048
+
+__global__ void radix_hist_kernel(const u64* __restrict__ keys, int64_t n, int shift,
+                                  uint32_t* counts, int nblk) {
+    __shared__ uint32_t h[256];
+    int t = threadIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int j = 0; j < 8; j++) {
+        int64_t i = base + j * 256 + t;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)t * nblk + blockIdx.x] = h[t];
+}
+
+__global__ void radix_scatter_kernel(const u64* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                     u64* __restrict__ kout, uint32_t* __restrict__ vout,
+                                     int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                     int nblk) {
+    __shared__ uint32_t goff[256];
+    __shared__ uint32_t run[256];
+    __shared__ uint16_t wcnt[8][257];
+    int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    goff[t] = offs[(int64_t)t * nblk + blockIdx.x];
+    run[t] = 0;
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int j = 0; j < 8; j++) {
+        for (int x = t; x < 8 * 257; x += 256) (&wcnt[0][0])[x] = 0;
+        __syncthreads();
+        int64_t i = base + j * 256 + t;
+        bool valid = i < n;
+        u64 k = valid ? kin[i] : 0ull;
+        uint32_t v = valid ? vin[i] : 0u;
+        int d = valid ? (int)((k >> shift) & 255) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int lrank = __popc(peers & ((1u << lane) - 1u));
+        if (lane == __ffs(peers) - 1) wcnt[w][d] = (uint16_t)__popc(peers);
+        __syncthreads();
+        {
+            uint32_t acc = run[t];
+            for (int ww = 0; ww < 8; ww++) {
+                uint32_t c = wcnt[ww][t];
+                wcnt[ww][t] = (uint16_t)acc;
+                acc += c;
+            }
+            run[t] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t p = goff[d] + wcnt[w][d] + (uint32_t)lrank;
+            kout[p] = k;
+            vout[p] = v;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t radix_sort_pairs(u64* keys, uint32_t* vals, int64_t n, int bits, const Scratch& s,
+                             cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+    u64* k2 = (u64*)s.get(n * sizeof(u64));
+    uint32_t* v2 = (uint32_t*)s.get(n * sizeof(uint32_t));
+    uint32_t* counts = (uint32_t*)s.get((size_t)256 * nblk * sizeof(uint32_t));
+    cudaError_t e = cudaSuccess;
+    if (!k2 || !v2 || !counts) e = cudaErrorMemoryAllocation;
+    u64 *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes && !e; p++) {
+        radix_hist_kernel<<<nblk, 256, 0, st>>>(ka, n, 8 * p, counts, nblk); note_launch();
+        e = cudaGetLastError();
+        if (!e) e = exclusive_scan_u32(counts, (int64_t)256 * nblk, s, st);
+        if (!e) {
+            radix_scatter_kernel<<<nblk, 256, 0, st>>>(ka, va, kb, vb, n, 8 * p, counts, nblk); note_launch();
+            e = cudaGetLastError();
+        }
+        u64* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+    if (!e && ka != keys) {
+        e = cudaMemcpyAsync(keys, ka, n * sizeof(u64), cudaMemcpyDeviceToDevice, st);
+        if (!e) e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    }
+    s.put(counts);
+    s.put(v2);
+    s.put(k2);
+    return e;
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void gather_kernel(const int32_t* __restrict__ xyz, const uint8_t* __restrict__ rgb,
+                              const float* __restrict__ nrm, const uint32_t* __restrict__ perm,
+                              int64_t n, int4* __restrict__ pos, uchar4* __restrict__ rgb_s,
+                              float4* __restrict__ nrm_s) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t i = perm[s];
+    pos[s] = make_int4(xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2],
+                       (int)i);
+    if (rgb_s) {
+        rgb_s[s] = make_uchar4(rgb[3 * (int64_t)i], rgb[3 * (int64_t)i + 1],
+                               rgb[3 * (int64_t)i + 2], 0);
+    }
+    if (nrm_s) {
+        nrm_s[s] = make_float4(nrm[3 * (int64_t)i], nrm[3 * (int64_t)i + 1],
+                               nrm[3 * (int64_t)i + 2], 0.f);
+    }
+}
+
+cudaError_t launch_gather(const int32_t* xyz, const uint8_t* rgb, const float* nrm,
+                          const uint32_t* perm, int64_t n, int4* pos, uchar4* rgb_s,
+                          float4* nrm_s, cudaStream_t st) {
+    gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        xyz, rgb_s ? rgb : nullptr, nrm_s ? nrm : nullptr, perm, n, pos, rgb_s, nrm_s); note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void gather_nrm_kernel(const float* __restrict__ nrm, const int4* __restrict__ pos,
+                                  int64_t n, float4* __restrict__ out) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int64_t i = pos[s].w;
+    out[s] = make_float4(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.f);
+}
+
+cudaError_t launch_gather_nrm(const float* nrm, const int4* pos, int64_t n, float4* out,
+                              cudaStream_t st) {
+    gather_nrm_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrm, pos, n, out); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ leaf levels
+// A level-L cell holding s has more than T points iff some window of T+1
+// consecutive Morton positions around s shares the level-L prefix.  With
+// Ls(j) = smallest level at which code[j] and code[j+T] share a cell, the
+// leaf level of s is min over j in [s-T, s] of Ls(j), minus one.
+__global__ void leaf_level_kernel(const u64* __restrict__ code, int64_t n, int T, int B,
+                                  uint8_t* __restrict__ leaf) {
+    extern __shared__ uint8_t ls[];
+    int64_t b0 = (int64_t)blockIdx.x * 256;
+    for (int x = threadIdx.x; x < 256 + T; x += 256) {
+        int64_t j = b0 - T + x;
+        uint8_t v = 255;
+        if (j >= 0 && j + T < n) {
+            u64 d = code[j] ^ code[j + T];
+            v = d == 0 ? 0 : (uint8_t)((63 - __clzll((long long)d)) / 3 + 1);
+        }
+        ls[x] = v;
+    }
+    __syncthreads();
+    int64_t i = b0 + threadIdx.x;
+    if (i >= n) return;
+    int mn = 255;
+    for (int x = 0; x <= T; x++) mn = min(mn, (int)ls[threadIdx.x + x]);
+    int L = mn == 255 ? B : (mn > 0 ? mn - 1 : 0);
+    if (L > B) L = B;
+    leaf[i] = (uint8_t)L;
+}
+
+cudaError_t launch_leaf_levels(const u64* code, int64_t n, int T, int B, uint8_t* leaf,
+                               cudaStream_t st) {
+    leaf_level_kernel<<<(unsigned)((n + 255) / 256), 256, 256 + T, st>>>(code, n, T, B, leaf); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ cell table
+__device__ inline bool run_head(const u64* code, int64_t i, int L) {
+    return i == 0 || (code[i - 1] >> (3 * L)) != (code[i] >> (3 * L));
+}
+__device__ inline bool run_tail(const u64* code, int64_t i, int64_t n, int L) {
+    return i == n - 1 || (code[i + 1] >> (3 * L)) != (code[i] >> (3 * L));
+}
+
+__global__ void node_count_kernel(const u64* __restrict__ code, const uint8_t* __restrict__ leaf,
+                                  int64_t n, int B, unsigned long long* count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned c = 0;
+    if (i < n) {
+        for (int L = leaf[i]; L <= B; L++) c += run_head(code, i, L);
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+cudaError_t launch_node_count(const u64* code, const uint8_t* leaf, int64_t n, int B,
+                              unsigned long long* count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e) return e;
+    node_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(code, leaf, n, B, count); note_launch();
+    return cudaGetLastError();
+}
+
+__device__ inline long long hash_insert(HashSlot* tab, u64 mask, u64 key) {
+    u64 h = mix64(key) & mask;
+    for (u64 it = 0; it <= mask; it++) {
+        u64 prev = atomicCAS(&tab[h].key, PD_EMPTY_KEY, key);
+        if (prev == PD_EMPTY_KEY || prev == key) return (long long)h;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__global__ void node_insert_kernel(const u64* __restrict__ code, const uint8_t* __restrict__ leaf,
+                                   int64_t n, int B, HashSlot* tab, u64 mask) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int L = leaf[i]; L <= B; L++) {
+        bool h = run_head(code, i, L), t = run_tail(code, i, n, L);
+        if (!h && !t) continue;
+        u64 prefix = code[i] >> (3 * L);
+        long long slot = hash_insert(tab, mask, cell_key(prefix, L, B));
+        if (slot < 0) continue;  // table sized at 2x the node count: cannot fill
+        if (h) tab[slot].b = (uint32_t)i;
+        if (t) tab[slot].e = (uint32_t)(i + 1);
+    }
+}
+
+cudaError_t launch_node_insert(const u64* code, const uint8_t* leaf, int64_t n, int B,
+                               HashSlot* tab, u64 mask, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(tab, 0, (mask + 1) * sizeof(HashSlot), st);
+    if (e) return e;
+    node_insert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(code, leaf, n, B, tab, mask); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ groups
+// Range [b, e) of the leaf that holds Morton position s.
+__device__ inline bool leaf_range(const GridView& g, int64_t s, uint32_t& b, uint32_t& e) {
+    int L = g.leaf[s];
+    return hash_find(g.hash, g.hmask, cell_key(g.code[s] >> (3 * L), L, g.B), b, e);
+}
+
+__global__ void leaf_groups_kernel(GridView g, int64_t n, int4* groups, int* ngroups) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t b, e;
+    if (!leaf_range(g, s, b, e)) return;
+    if (((uint32_t)s - b) % 32 != 0) return;
+    int slot = atomicAdd(ngroups, 1);
+    int cnt = (int)min((uint32_t)32, e - (uint32_t)s);
+    groups[slot] = make_int4((int)s, cnt, (int)g.leaf[s], 0);
+}
+
+cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* ngroups,
+                               cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(ngroups, 0, sizeof(int), st);
+    if (e) return e;
+    leaf_groups_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, groups, ngroups); note_launch();
+    return cudaGetLastError();
+}
+
+// list groups: entry t starts a group when its (leaf, 32-chunk of the leaf
+// range) differs from entry t-1's.
+__global__ void list_head_kernel(GridView g, const int* __restrict__ list, int64_t len,
+                                 uint8_t* head, u64* chunk_id) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    int s = list[t];
+    uint32_t b, e;
+    u64 id = ~0ull;
+    if (leaf_range(g, s, b, e)) id = ((u64)b << 32) | (((uint32_t)s - b) >> 5);
+    chunk_id[t] = id;
+}
+
+__global__ void list_head_flag_kernel(const u64* __restrict__ chunk_id, int64_t len,
+                                      uint8_t* head) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    head[t] = (t == 0 || chunk_id[t] != chunk_id[t - 1]) ? 1 : 0;
+}
+
+__global__ void list_group_fill_kernel(GridView g, const int* __restrict__ list, int64_t len,
+                                       const int* __restrict__ heads, const int* nheads,
+                                       int4* groups) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int nh = *nheads;
+    if (t >= nh) return;
+    int off = heads[t];
+    int end = t + 1 < nh ? heads[t + 1] : (int)len;
+    int s = list[off];
+    groups[t] = make_int4(off, end - off, (int)g.leaf[s], 1);
+}
+
+cudaError_t launch_list_groups(const GridView& g, const int* list, int64_t len, int4* groups,
+                               int* ngroups, const Scratch& s, cudaStream_t st) {
+    if (len <= 0) return cudaMemsetAsync(ngroups, 0, sizeof(int), st);
+    uint8_t* head = (uint8_t*)s.get(len);
+    u64* cid = (u64*)s.get(len * sizeof(u64));
+    int* heads = (int*)s.get(len * sizeof(int));
+    cudaError_t e = (head && cid && heads) ? cudaSuccess : cudaErrorMemoryAllocation;
+    unsigned nb = (unsigned)((len + 255) / 256);
+    if (!e) {
+        list_head_kernel<<<nb, 256, 0, st>>>(g, list, len, head, cid); note_launch();
+        list_head_flag_kernel<<<nb, 256, 0, st>>>(cid, len, head); note_launch();
+        e = cudaGetLastError();
+    }
+    if (!e) e = stable_compact(head, len, heads, ngroups, s, st);
+    if (!e) {
+        list_group_fill_kernel<<<nb, 256, 0, st>>>(g, list, len, heads, ngroups, groups); note_launch();
+        e = cudaGetLastError();
+    }
+    s.put(heads);
+    s.put(cid);
+    s.put(head);
+    return e;
+}
+
+// ------------------------------------------------------------------ compaction
+__global__ void compact_count_kernel(const uint8_t* __restrict__ flag, int64_t n,
+                                     uint32_t* counts) {
+    __shared__ uint32_t ws[8];
+    int64_t base = (int64_t)blockIdx.x * 1024;
+    uint32_t c = 0;
+    for (int j = 0; j < 4; j++) {
+        int64_t i = base + j * 256 + threadIdx.x;
+        c += (i < n && flag[i]) ? 1u : 0u;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < 8; w++) s += ws[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+__global__ void compact_write_kernel(const uint8_t* __restrict__ flag, int64_t n,
+                                     const uint32_t* __restrict__ offs, int nblk, int* out,
+                                     int* count) {
+    __shared__ uint32_t ws[8];
+    __shared__ uint32_t run;
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) run = offs[blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * 1024;
+    for (int j = 0; j < 4; j++) {
+        __syncthreads();
+        int64_t i = base + j * 256 + t;
+        bool f = i < n && flag[i];
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) ws[w] = __popc(bal);
+        __syncthreads();
+        uint32_t off = run;
+        for (int ww = 0; ww < w; ww++) off += ws[ww];
+        if (f) out[off + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+        __syncthreads();
+        if (t == 0) {
+            uint32_t s = 0;
+            for (int ww = 0; ww < 8; ww++) s += ws[ww];
+            run += s;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == nblk - 1 && t == 0) *count = (int)run;
+}
+
+cudaError_t stable_compact(const uint8_t* flag, int64_t n, int* out, int* count,
+                           const Scratch& s, cudaStream_t st) {
+    if (n <= 0) return cudaMemsetAsync(count, 0, sizeof(int), st);
+    int nblk = (int)((n + 1023) / 1024);
+    uint32_t* offs = (uint32_t*)s.get((size_t)nblk * sizeof(uint32_t));
+    if (!offs) return cudaErrorMemoryAllocation;
+    compact_count_kernel<<<nblk, 256, 0, st>>>(flag, n, offs); note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = exclusive_scan_u32(offs, nblk, s, st);
+    if (!e) {
+        compact_write_kernel<<<nblk, 256, 0, st>>>(flag, n, offs, nblk, out, count); note_launch();
+        e = cudaGetLastError();
+    }
+    s.put(offs);
+    return e;
+}
+
+}  // namespace pd

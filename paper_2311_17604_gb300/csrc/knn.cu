@@ -1,0 +1,332 @@
+// knn.cu -- exact k-nearest-neighbour search and cost (Eq. 10 / Eq. 11).
+//
+// One warp serves one group of <= 32 query points that share an octree leaf
+// of level L.  The warp resolves the 3x3x3 level-L cells around the leaf in
+// the hashed cell table (the own cell first), then scans their points in
+// chunks of 32: every lane loads one candidate (a coalesced 16-byte int4
+// load of {x, y, z, index}), the chunk is staged in shared memory, and every
+// lane streams the whole chunk against its own query, keeping the S smallest
+// (d^2, position) pairs in registers.  Squared distances are exact integers:
+// uint32 when every coordinate difference in the searched cells is at most
+// 2^15 mm, uint64 otherwise.  A cell is skipped when its box is farther than
+// the current bound for every lane.  Exactness: every point outside the
+// searched cube lies at least g from the query (g = distance to the cube's
+// faces); when the bound that matters is below g^2 the lane is done,
+// otherwise the search repeats one level up (a cube of twice the size).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+namespace pd {
+
+#define FULLM 0xffffffffu
+
+template <int S>
+struct TopList {
+    u64 d[S];
+    int id[S];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            d[i] = ~0ull;
+            id[i] = 0x7fffffff;
+        }
+    }
+    __device__ __forceinline__ void insert(u64 dd, int j) {
+        d[S - 1] = dd;
+        id[S - 1] = j;
+#pragma unroll
+        for (int i = S - 1; i > 0; i--) {
+            bool sw = d[i] < d[i - 1] || (d[i] == d[i - 1] && id[i] < id[i - 1]);
+            u64 a = d[i], b = d[i - 1];
+            int x = id[i], y = id[i - 1];
+            d[i - 1] = sw ? a : b;
+            d[i] = sw ? b : a;
+            id[i - 1] = sw ? x : y;
+            id[i] = sw ? y : x;
+        }
+    }
+    __device__ __forceinline__ u64 at(int r) const {
+        u64 v = d[0];
+#pragma unroll
+        for (int i = 1; i < S; i++)
+            if (i == r) v = d[i];
+        return v;
+    }
+};
+
+__device__ inline u64 box_d2(int ux, int uy, int uz, int bx, int by, int bz, int sh) {
+    long long q[3] = {ux, uy, uz};
+    int c[3] = {bx, by, bz};
+    u64 s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        long long lo = (long long)c[a] << sh;
+        long long hi = ((long long)(c[a] + 1) << sh) - 1;
+        long long d = q[a] < lo ? lo - q[a] : (q[a] > hi ? q[a] - hi : 0);
+        s += (u64)(d * d);
+    }
+    return s;
+}
+
+// Squared distance from the query to the outside of the level-L cube of
+// cells [c-1, c+1]; ~0 when the cube holds the whole cloud.
+__device__ inline u64 gap2(const GridView& g, int ux, int uy, int uz, int L, int cx, int cy,
+                           int cz) {
+    int sh = L + g.shift;
+    long long q[3] = {ux, uy, uz};
+    int c[3] = {cx, cy, cz};
+    int m[3] = {g.umax.x, g.umax.y, g.umax.z};
+    long long best = -1;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        long long lo = (long long)(c[a] - 1) << sh;
+        long long hi = (long long)(c[a] + 2) << sh;
+        if (lo > 0) {
+            long long d = q[a] - lo + 1;
+            if (best < 0 || d < best) best = d;
+        }
+        if (hi <= m[a]) {
+            long long d = hi - q[a];
+            if (best < 0 || d < best) best = d;
+        }
+    }
+    return best < 0 ? ~0ull : (u64)best * (u64)best;
+}
+
+__device__ inline double nbr_weight(const KnnArgs& a, int q, int j) {
+    if (a.term == 1) {  // colour deviation
+        uchar4 p = a.rgb[q], r = a.rgb[j];
+        double dr = (double)p.x - (double)r.x;
+        double dg = (double)p.y - (double)r.y;
+        double db = (double)p.z - (double)r.z;
+        double s = __dmul_rn(dr, dr);
+        s = __dadd_rn(s, __dmul_rn(dg, dg));
+        s = __dadd_rn(s, __dmul_rn(db, db));
+        double dist = __dsqrt_rn(s);
+        double scale = __dmul_rn(255.0, __dsqrt_rn(3.0));
+        return __dsub_rn(1.0, __dmul_rn(a.weight, __ddiv_rn(dist, scale)));
+    }
+    if (a.term == 2) {  // orientation, Eq. 13 with |n_p . n_q|
+        float4 p = a.nrm[q], r = a.nrm[j];
+        double d = __dmul_rn((double)p.x, (double)r.x);
+        d = __dadd_rn(d, __dmul_rn((double)p.y, (double)r.y));
+        d = __dadd_rn(d, __dmul_rn((double)p.z, (double)r.z));
+        return __dsub_rn(1.0, __dmul_rn(a.weight, __dsub_rn(1.0, fabs(d))));
+    }
+    return 1.0;
+}
+
+template <int S>
+__device__ inline double cost_sum(const KnnArgs& a, int q, const TopList<S>& top, int k) {
+    double c = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; i++) {
+        if (i < k && top.d[i] != ~0ull) {
+            double w = nbr_weight(a, q, top.id[i]);
+            c = __dadd_rn(c, __ddiv_rn(w, (double)top.d[i]));
+        }
+    }
+    return c;
+}
+
+// Stream one range [b, e) of Morton positions against every lane's query.
+template <int S, int FILT, typename D>
+__device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, uint32_t b,
+                                           uint32_t e, int q, int4 qp, bool todo, u64 tp, int ti,
+                                           TopList<S>& top, int4* sp, u64* sk, int* so,
+                                           int lane) {
+    for (uint32_t c = b; c < e; c += 32) {
+        uint32_t j = c + lane;
+        int4 v = make_int4(0, 0, 0, -1);
+        if (j < e) {
+            v = g.pos[j];
+            bool ok = !a.alive || a.alive[j];
+            if (FILT != FILT_NONE) {
+                sk[lane] = a.prim[j];
+                so[lane] = v.w;
+            }
+            v.w = ok ? (int)j : -1;
+        }
+        sp[lane] = v;
+        __syncwarp();
+        int m = (int)min(32u, e - c);
+        if (todo) {
+            D worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
+            for (int t = 0; t < m; t++) {
+                int4 cv = sp[t];
+                if (cv.w < 0 || cv.w == q) continue;
+                if (FILT != FILT_NONE) {
+                    if (!key_gt(tp, ti, sk[t], so[t])) continue;  // keep keys below threshold
+                }
+                int dx = cv.x - qp.x, dy = cv.y - qp.y, dz = cv.z - qp.z;
+                D dd;
+                if (sizeof(D) == 4) {
+                    dd = (D)(dx * dx) + (D)(dy * dy) + (D)(dz * dz);
+                } else {
+                    dd = (D)((long long)dx * dx) + (D)((long long)dy * dy) + (D)((long long)dz * dz);
+                }
+                if (dd < worst || (dd == worst && cv.w < top.id[S - 1])) {
+                    top.insert((u64)dd, cv.w);
+                    worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int S, int FILT>
+__global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs a) {
+    __shared__ int4 s_p[PD_WARPS][32];
+    __shared__ u64 s_k[PD_WARPS][32];
+    __shared__ int s_o[PD_WARPS][32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int gid = blockIdx.x * PD_WARPS + w;
+    if (gid >= a.ngroups) return;
+    int4 G = a.groups[gid];
+    int cnt = G.y;
+    int L = G.z;
+    int q = -1;
+    if (lane < cnt) q = a.list ? a.list[G.x + lane] : G.x + lane;
+    int q0 = a.list ? a.list[G.x] : G.x;
+    u64 c0 = g.code[q0];
+    int4 qp = q >= 0 ? g.pos[q] : make_int4(0, 0, 0, 0);
+    int ux = qp.x - g.origin.x, uy = qp.y - g.origin.y, uz = qp.z - g.origin.z;
+    u64 tp = 0;
+    int ti = 0;
+    if (FILT == FILT_BELOW_SELF && q >= 0) {
+        tp = a.prim[q];
+        ti = qp.w;
+    } else if (FILT == FILT_BELOW_TAU) {
+        tp = a.tau_prim;
+        ti = a.tau_idx;
+    }
+    // exactness bound: the R-th smallest distance must be exact
+    const int R = (FILT == FILT_NONE && a.density_k1) ? 1 : a.k;
+    TopList<S> top;
+    top.init();
+    bool todo = q >= 0;
+    while (__any_sync(FULLM, todo)) {
+        int sh = 3 * L;
+        int cx = (int)compact3(c0 >> sh), cy = (int)compact3(c0 >> (sh + 1)),
+            cz = (int)compact3(c0 >> (sh + 2));
+        if (L >= g.B) cx = cy = cz = 0;
+        int o = (lane + 13) % 27;
+        int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+        uint32_t rb = 0, re = 0;
+        int rl = L, rt = 0;
+        if (lane < 27) rt = resolve_cell(g, L, cx + dx, cy + dy, cz + dz, rb, re, &rl);
+        for (int j = 0; j < 27; j++) {  // a coarse leaf reached from two cells is scanned once
+            uint32_t bj = __shfl_sync(FULLM, rb, j);
+            int tj = __shfl_sync(FULLM, rt, j);
+            if (j < lane && rt == 2 && tj == 2 && bj == rb) rt = 0;
+        }
+        int bx = 0, by = 0, bz = 0;
+        if (rt) {
+            bx = (cx + dx) >> (rl - L);
+            by = (cy + dy) >> (rl - L);
+            bz = (cz + dz) >> (rl - L);
+        }
+        for (int r = 0; r < 27; r++) {
+            int tr = __shfl_sync(FULLM, rt, r);
+            if (!tr) continue;
+            uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
+            int lv = __shfl_sync(FULLM, rl, r);
+            int bxr = __shfl_sync(FULLM, bx, r), byr = __shfl_sync(FULLM, by, r),
+                bzr = __shfl_sync(FULLM, bz, r);
+            bool skip = true;
+            if (todo) {
+                u64 bound = top.at(R - 1);
+                skip = bound != ~0ull && box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift) > bound;
+            }
+            if (__all_sync(FULLM, skip)) continue;
+            if (lv + g.shift <= 13)
+                scan_range<S, FILT, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
+                                              s_o[w], lane);
+            else
+                scan_range<S, FILT, u64>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
+                                         s_o[w], lane);
+        }
+        if (todo) {
+            u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
+            u64 bound = top.at(R - 1);
+            if (gg == ~0ull || bound < gg) {
+                todo = false;
+                int found = 0;
+#pragma unroll
+                for (int i = 0; i < S; i++) found += top.d[i] != ~0ull;
+                if (FILT == FILT_NONE) {
+                    if (a.density_k1) {
+                        u64 d0 = top.d[0];
+                        int shell = 0;
+#pragma unroll
+                        for (int i = 0; i < S; i++) {
+                            bool in = d0 != ~0ull && top.d[i] == d0;
+                            shell += in;
+                            a.nbr[(int64_t)q * S + i] = in ? top.id[i] : -1;
+                        }
+                        a.prim_out[q] = key_prim_d2(d0);
+                        a.rk2_out[q] = d0;
+                        a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0));
+                        if (a.cost_out)
+                            a.cost_out[q] = d0 == ~0ull ? 0.0 : __ddiv_rn(1.0, (double)d0);
+                    } else {
+                        int k = a.k;
+#pragma unroll
+                        for (int i = 0; i < S; i++)
+                            a.nbr[(int64_t)q * S + i] = top.d[i] != ~0ull ? top.id[i] : -1;
+                        double c = cost_sum<S>(a, q, top, k);
+                        a.prim_out[q] = key_prim_cost(c);
+                        u64 dk = top.at(k - 1);
+                        a.rk2_out[q] = dk;
+                        bool tie = found > k && top.at(k) == dk;
+                        a.flg_out[q] = (uint8_t)(tie ? 1 : 0);
+                        if (a.cost_out) a.cost_out[q] = c;
+                    }
+                } else if (FILT == FILT_BELOW_SELF) {
+                    if (a.density_k1) {
+                        a.fprim_out[q] = key_prim_d2(top.d[0]);
+                    } else {
+                        a.fprim_out[q] = key_prim_cost(cost_sum<S>(a, q, top, a.k));
+                    }
+                } else {
+                    a.lam_out[q] = top.at(a.k - 1);
+                }
+            } else {
+                top.init();
+            }
+        }
+        L++;
+    }
+}
+
+template <int S, int FILT>
+static cudaError_t launch_knn_t(const GridView& g, const KnnArgs& a, cudaStream_t st) {
+    if (a.ngroups <= 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((a.ngroups + PD_WARPS - 1) / PD_WARPS);
+    knn_kernel<S, FILT><<<blocks, PD_WARPS * 32, 0, st>>>(g, a); note_launch();
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t launch_knn_s(const GridView& g, const KnnArgs& a, cudaStream_t st) {
+    switch (a.filter) {
+        case FILT_NONE: return launch_knn_t<S, FILT_NONE>(g, a, st);
+        case FILT_BELOW_SELF: return launch_knn_t<S, FILT_BELOW_SELF>(g, a, st);
+        default: return launch_knn_t<S, FILT_BELOW_TAU>(g, a, st);
+    }
+}
+
+cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st) {
+    switch (a.S) {
+        case 4: return launch_knn_s<4>(g, a, st);
+        case 8: return launch_knn_s<8>(g, a, st);
+        case 17: return launch_knn_s<17>(g, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pd

@@ -1,0 +1,90 @@
+// pd_kernels.h -- host-side launchers of the libpd kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+typedef unsigned long long u64;
+
+// Scratch memory handed to launchers by the caller (the grid object).
+struct Scratch {
+    void* (*alloc)(void* self, size_t bytes);
+    void (*free)(void* self, void* p);
+    void* self;
+    void* get(size_t bytes) const { return alloc(self, bytes); }
+    void put(void* p) const { free(self, p); }
+};
+
+// ---------------------------------------------------------------- grid.cu
+cudaError_t launch_bbox(const int32_t* xyz, int64_t n, int* out6, cudaStream_t st);
+cudaError_t launch_morton(const int32_t* xyz, int64_t n, int3 origin, int shift, u64* keys,
+                          uint32_t* vals, cudaStream_t st);
+// Stable LSD radix sort of (keys, vals) on bits [0, bits); results land in
+// keys/vals (ping-pong through tmp buffers).
+cudaError_t radix_sort_pairs(u64* keys, uint32_t* vals, int64_t n, int bits, const Scratch& s,
+                             cudaStream_t st);
+cudaError_t exclusive_scan_u32(uint32_t* data, int64_t len, const Scratch& s, cudaStream_t st);
+cudaError_t launch_gather(const int32_t* xyz, const uint8_t* rgb, const float* nrm,
+                          const uint32_t* perm, int64_t n, int4* pos, uchar4* rgb_s,
+                          float4* nrm_s, cudaStream_t st);
+cudaError_t launch_gather_nrm(const float* nrm, const int4* pos, int64_t n, float4* out,
+                              cudaStream_t st);
+cudaError_t launch_leaf_levels(const u64* code, int64_t n, int T, int B, uint8_t* leaf,
+                               cudaStream_t st);
+cudaError_t launch_node_count(const u64* code, const uint8_t* leaf, int64_t n, int B,
+                              unsigned long long* count, cudaStream_t st);
+cudaError_t launch_node_insert(const u64* code, const uint8_t* leaf, int64_t n, int B,
+                               HashSlot* tab, u64 mask, cudaStream_t st);
+// Groups of <= 32 points of one leaf, for every point (full mode).
+cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* ngroups,
+                               cudaStream_t st);
+// Groups over an ordered list of Morton positions: consecutive entries of the
+// same leaf chunk (32 positions of the leaf range) form one group.
+cudaError_t launch_list_groups(const GridView& g, const int* list, int64_t len, int4* groups,
+                               int* ngroups, const Scratch& s, cudaStream_t st);
+// Stable compaction: out = ascending s with flag[s] != 0; *count on device.
+cudaError_t stable_compact(const uint8_t* flag, int64_t n, int* out, int* count,
+                           const Scratch& s, cudaStream_t st);
+
+// ---------------------------------------------------------------- knn.cu
+enum { FILT_NONE = 0, FILT_BELOW_SELF = 1, FILT_BELOW_TAU = 2 };
+
+struct KnnArgs {
+    const int4* groups;
+    int ngroups;
+    const int* list;          // list mode: group.x is an offset into list
+    const uint8_t* alive;     // NULL = every point live
+    const u64* prim;          // keys (filter modes)
+    int filter;
+    u64 tau_prim;
+    int tau_idx;
+    int k;
+    int S;                    // stored neighbours (template width)
+    int density_k1;           // integer-ordered k = 1 density cost
+    int term;
+    double weight;
+    const uchar4* rgb;
+    const float4* nrm;
+    // outputs (full / re-query mode)
+    int* nbr;                 // n x S Morton positions
+    u64* prim_out;            // key primary
+    u64* rk2_out;             // k-th squared distance
+    uint8_t* flg_out;
+    double* cost_out;         // cost in Morton order (optional)
+    // outputs (filter modes)
+    u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
+    u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
+};
+cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------- rounds.cu
+struct SelectResult {
+    u64 prim;
+    int idx;
+};
+
+}  // namespace pd

@@ -1,0 +1,275 @@
+"""Python binding of libpd (include/pd.h): argument marshalling only.
+
+Every step of the decimation runs in the library's CUDA kernels; this module
+only converts torch tensors / numpy arrays to pointers, passes the current
+CUDA stream, and routes the library's device allocations through PyTorch's
+caching allocator.  The CUDA library must be built (``build.build()``);
+importing this module on a machine without it raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpd.so")
+
+PD_OK, PD_EINVAL, PD_ERANGE, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EINTERNAL = range(7)
+PD_TERM_NONE, PD_TERM_COLOR, PD_TERM_ORIENT = 0, 1, 2
+PD_KMAX = 16
+
+EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
+            "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
+            "pd_grid_stats", "pd_decimate_host"]
+
+
+class PdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_strerror(code), code, msg))
+        self.code = code
+
+
+class pd_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p)),
+                ("user", ctypes.c_void_p)]
+
+
+class pd_grid_params(ctypes.Structure):
+    _fields_ = [("leaf_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class pd_cost_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("term", ctypes.c_int32), ("weight", ctypes.c_double),
+                ("normals_dev", ctypes.c_void_p), ("band", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class pd_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("grid_builds", ctypes.c_int32), ("dup_removed", ctypes.c_int64),
+                ("requeries", ctypes.c_int64), ("filtered_queries", ctypes.c_int64),
+                ("danger_queries", ctypes.c_int64), ("ms_total", ctypes.c_double),
+                ("ms_knn", ctypes.c_double), ("ms_build", ctypes.c_double),
+                ("ms_knn_first", ctypes.c_double), ("q_first", ctypes.c_int64),
+                ("ms_knn_requery", ctypes.c_double), ("ms_rules", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libpd.so is not built: run paper_2311_17604_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64 = ctypes.c_void_p, ctypes.c_int64
+        L.pd_ctx_create.argtypes = [ctypes.POINTER(pd_allocator), ctypes.POINTER(P)]
+        L.pd_ctx_destroy.argtypes = [P]
+        L.pd_ctx_destroy.restype = None
+        L.pd_strerror.argtypes = [ctypes.c_int]
+        L.pd_strerror.restype = ctypes.c_char_p
+        L.pd_last_error.argtypes = [P]
+        L.pd_last_error.restype = ctypes.c_char_p
+        L.pd_build_grid.argtypes = [P, P, P, I64, ctypes.POINTER(pd_grid_params), P,
+                                    ctypes.POINTER(P)]
+        L.pd_grid_free.argtypes = [P]
+        L.pd_knn_cost.argtypes = [P, ctypes.POINTER(pd_cost_params), P, P, P]
+        L.pd_decimate_count.argtypes = [P, ctypes.POINTER(pd_cost_params), I64, P, P]
+        L.pd_decimate_ratio.argtypes = [P, ctypes.POINTER(pd_cost_params), ctypes.c_double, P, P]
+        L.pd_grid_stats.argtypes = [P, ctypes.POINTER(pd_stats)]
+        L.pd_decimate_host.argtypes = [P, P, P, P, I64, ctypes.POINTER(pd_cost_params), I64, P,
+                                       P, ctypes.POINTER(pd_stats)]
+        for f in EXPORTED:
+            if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
+                getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return lib().pd_strerror(code).decode()
+    except Exception:
+        return "error"
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """pd_ctx with PyTorch's caching allocator as the device allocator."""
+
+    def __init__(self, use_torch_allocator: bool = True):
+        self._keep = []
+        a = None
+        if use_torch_allocator:
+            torch = _torch()
+
+            @ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+            def _alloc(user, nbytes, stream):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+                except Exception:
+                    return None
+
+            @ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+            def _free(user, ptr, stream):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            a = pd_allocator(_alloc, _free, None)
+            self._keep += [_alloc, _free, a]
+        h = ctypes.c_void_p()
+        rc = lib().pd_ctx_create(ctypes.byref(a) if a is not None else None, ctypes.byref(h))
+        if rc:
+            raise PdError(rc, "pd_ctx_create")
+        self.h = h
+
+    def error(self) -> str:
+        return lib().pd_last_error(self.h).decode()
+
+    def check(self, rc, what):
+        if rc:
+            raise PdError(rc, "%s: %s" % (what, self.error()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cost_params(k=1, term=PD_TERM_NONE, weight=0.0, normals=None, band=0.0):
+    return pd_cost_params(int(k), int(term), float(weight), _ptr(normals), float(band))
+
+
+class Grid:
+    """A resident cloud (pd_grid) built from a device int32 [n,3] tensor."""
+
+    def __init__(self, ctx: Context, xyz, rgb=None, leaf_max=0, stream=None):
+        torch = _torch()
+        assert xyz.is_cuda and xyz.dtype == torch.int32 and xyz.dim() == 2 and xyz.shape[1] == 3
+        xyz = xyz.contiguous()
+        if rgb is not None:
+            assert rgb.is_cuda and rgb.dtype == torch.uint8
+            rgb = rgb.contiguous()
+        self.ctx = ctx
+        self.n = int(xyz.shape[0])
+        h = ctypes.c_void_p()
+        p = pd_grid_params(int(leaf_max))
+        rc = lib().pd_build_grid(ctx.h, _ptr(xyz), _ptr(rgb), self.n, ctypes.byref(p),
+                                 _stream_ptr(stream), ctypes.byref(h))
+        ctx.check(rc, "pd_build_grid")
+        self.h = h
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().pd_grid_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = pd_stats()
+        self.ctx.check(lib().pd_grid_stats(self.h, ctypes.byref(s)), "pd_grid_stats")
+        return s.as_dict()
+
+
+def pd_build_grid(ctx, xyz, rgb=None, leaf_max=0, stream=None) -> Grid:
+    return Grid(ctx, xyz, rgb, leaf_max, stream)
+
+
+def pd_knn_cost(grid: Grid, k=1, term=PD_TERM_NONE, weight=0.0, normals=None, cost=None,
+                knn=None, stream=None):
+    """Cost (float64 [n]) and k nearest input indices (int32 [n,k]) of every point."""
+    torch = _torch()
+    dev = torch.device("cuda")
+    if cost is None:
+        cost = torch.empty(grid.n, dtype=torch.float64, device=dev)
+    if knn is None:
+        knn = torch.empty((grid.n, k), dtype=torch.int32, device=dev)
+    cp = cost_params(k, term, weight, normals)
+    rc = lib().pd_knn_cost(grid.h, ctypes.byref(cp), _ptr(cost), _ptr(knn), _stream_ptr(stream))
+    grid.ctx.check(rc, "pd_knn_cost")
+    return cost, knn
+
+
+def pd_decimate_count(grid: Grid, m, k=1, term=PD_TERM_NONE, weight=0.0, normals=None,
+                      keep=None, band=0.0, stream=None):
+    """Greedy decimation to exactly m points; returns the uint8 keep mask [n]."""
+    torch = _torch()
+    if keep is None:
+        keep = torch.empty(grid.n, dtype=torch.uint8, device="cuda")
+    cp = cost_params(k, term, weight, normals, band)
+    rc = lib().pd_decimate_count(grid.h, ctypes.byref(cp), int(m), _ptr(keep),
+                                 _stream_ptr(stream))
+    grid.ctx.check(rc, "pd_decimate_count")
+    return keep
+
+
+def pd_decimate_ratio(grid: Grid, ratio, k=1, term=PD_TERM_NONE, weight=0.0, normals=None,
+                      keep=None, band=0.0, stream=None):
+    torch = _torch()
+    if keep is None:
+        keep = torch.empty(grid.n, dtype=torch.uint8, device="cuda")
+    cp = cost_params(k, term, weight, normals, band)
+    rc = lib().pd_decimate_ratio(grid.h, ctypes.byref(cp), float(ratio), _ptr(keep),
+                                 _stream_ptr(stream))
+    grid.ctx.check(rc, "pd_decimate_ratio")
+    return keep
+
+
+def pd_decimate_host(ctx: Context, xyz: np.ndarray, m, k=1, term=PD_TERM_NONE, weight=0.0,
+                     rgb=None, normals=None, keep=None, band=0.0, stream=None):
+    """End to end on host arrays (numpy, ideally pinned): returns (keep, stats)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    n = xyz.shape[0]
+    if keep is None:
+        keep = np.empty(n, dtype=np.uint8)
+    rgb = None if rgb is None else np.ascontiguousarray(rgb, dtype=np.uint8)
+    normals = None if normals is None else np.ascontiguousarray(normals, dtype=np.float32)
+    cp = cost_params(k, term, weight, None, band)
+    st = pd_stats()
+    rc = lib().pd_decimate_host(ctx.h, _ptr(xyz), _ptr(rgb), _ptr(normals), n, ctypes.byref(cp),
+                                int(m), _ptr(keep), _stream_ptr(stream), ctypes.byref(st))
+    ctx.check(rc, "pd_decimate_host")
+    return keep, st.as_dict()
