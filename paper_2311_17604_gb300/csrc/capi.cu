@@ -41,7 +41,7 @@ cudaError_t launch_kk_accept(const int*, const int*, int, const u64*, const u64*
                              int*, cudaStream_t);
 cudaError_t launch_danger(const GridView&, const int*, const int*, int, const u64*,
                           const uint8_t*, const uint8_t*, uint8_t*, const u64*, int, int2*, int*,
-                          int, int*, cudaStream_t);
+                          int, int*, unsigned long long*, cudaStream_t);
 cudaError_t launch_accept_above(const u64*, const int4*, const uint8_t*, int64_t, u64, int,
                                 uint8_t*, int*, int*, cudaStream_t);
 cudaError_t launch_pair_fix(const int2*, const int*, int, int, const uint8_t*, uint8_t*, int*,
@@ -119,7 +119,8 @@ struct pd_grid {
     unsigned long long* d_u64;   // [0] counts
     std::vector<void*> owned;
     pd_stats stats;
-    int trace;  // PD_TRACE set: one line per removal round on stderr
+    int trace;       // PD_TRACE set: one line per removal round on stderr
+    int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
 };
 
 namespace {
@@ -284,6 +285,7 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     g->ctx = ctx;
     g->st = (cudaStream_t)stream;
     g->trace = getenv("PD_TRACE") != nullptr;
+    g->max_rounds = getenv("PD_MAX_ROUNDS") ? atoi(getenv("PD_MAX_ROUNDS")) : 0;
     g->n = n;
     g->ng = n;
     g->T = T;
@@ -642,9 +644,6 @@ int select_rank(pd_grid* g, const u64* prim, const uint8_t* alive, int64_t r, in
     return rc;
 }
 
-bool sel_gt(const Sel& a, const Sel& b) {
-    return a.prim > b.prim || (a.prim == b.prim && a.idx > b.idx);
-}
 
 // Duplicate phase: coincident points beyond the smallest index of their
 // class are the first pops of the sequential greedy (their cost is +inf).
@@ -701,7 +700,13 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     rc = prepare_state(g, cp);
     if (rc) return rc;
     int k = cp->k;
-    double band = cp->band > 0 ? cp->band : 0.2;
+    // k >= 2 candidate band: fraction of the live points examined per round.
+    // It adapts to the cloud: halved when a round's danger analysis overflows
+    // or its yield is poor (the band then covers whole dense regions with no
+    // lower keys inside), grown again while yields stay high.  Any band gives
+    // the same result; only the number of rounds changes.
+    double band_max = cp->band > 0 ? cp->band : 0.05;
+    double band = band_max;
     int64_t live = g->n;
     // ---- duplicate phase
     int64_t nd = 0;
@@ -756,21 +761,30 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     while (live > m) {
         int64_t need = live - m;
         g->stats.rounds++;
+        if (g->max_rounds && g->stats.rounds > g->max_rounds) {
+            set_err(g->ctx, "pd_decimate: stopped after %s%lld rounds (PD_MAX_ROUNDS)", "",
+                    (long long)g->max_rounds);
+            return PD_EINTERNAL;
+        }
         if (g->stats.rounds > 1000000) {
             set_err(g->ctx, "pd_decimate: round limit reached%s (live = %lld)", "", live);
             return PD_EINTERNAL;
         }
-        Sel kst, bnd;
-        int64_t band_rank = std::max<int64_t>(1, (int64_t)(band * (double)live));
-        rc = select_rank(g, g->prim, g->alive, need, 0, &kst, nullptr);
-        if (rc) return rc;
-        Sel tau = kst;
-        if (!g->density_k1 && band_rank < need) {
-            // k >= 2: examine only the band_rank largest keys this round
-            rc = select_rank(g, g->prim, g->alive, band_rank, 0, &bnd, nullptr);
-            if (rc) return rc;
-            if (sel_gt(bnd, tau)) tau = bnd;
+        // k = 1: every key >= K* (the need-th largest) is examined.  k >= 2:
+        // only the r largest keys, r = min(band * live, need / 4) <= need, so
+        // the threshold is >= K* (condition R2 holds) and at least three
+        // quarters of the points still to be removed stay below it, where
+        // they shield candidates from farther sources (small search radii).
+        int64_t rank = need;
+        if (!g->density_k1) {
+            int64_t band_rank = (int64_t)(band * (double)live);
+            rank = std::max<int64_t>(1, std::min<int64_t>(band_rank, (need + 3) / 4));
         }
+        Sel tau;
+        rc = select_rank(g, g->prim, g->alive, rank, 0, &tau, nullptr);
+        if (rc) return rc;
+        int ncand_a = 0;
+        unsigned long long cap_over = 0;
         CK(cudaMemsetAsync(d + 4, 0, 4 * sizeof(int), g->st));
         int hc[4];
         if (g->density_k1) {
@@ -835,8 +849,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
                 }
                 CK(cudaMemcpyAsync(d + 7, &ndg, sizeof(int), cudaMemcpyHostToDevice, g->st));
                 CK(cudaMemsetAsync(d + 5, 0, 2 * sizeof(int), g->st));  // npairs, overflow
+                CK(cudaMemsetAsync(g->d_u64, 0, 4 * sizeof(u64), g->st));
                 CK(launch_danger(view_of(g), dgl, d + 7, ndg, g->prim, g->alive, inP, rej, lam,
-                                 k, pairs, d + 5, pair_cap, d + 6, g->st));
+                                 k, pairs, d + 5, pair_cap, d + 6, g->d_u64, g->st));
                 CK(cudaMemcpyAsync(hc, d + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
                 CK(cudaStreamSynchronize(g->st));
                 if (hc[2]) {
@@ -848,6 +863,18 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
                     continue;
                 }
                 int npairs = std::min(hc[1], pair_cap);
+                ncand_a = hc[0];
+                {
+                    unsigned long long dg[4];
+                    CK(cudaMemcpyAsync(dg, g->d_u64, sizeof(dg), cudaMemcpyDeviceToHost, g->st));
+                    CK(cudaStreamSynchronize(g->st));
+                    cap_over = dg[1];
+                    if (g->trace)
+                    fprintf(stderr, "pd   k>=2: tau %016llx:%d cand(A) %d fq %d sources %d pairs %d "
+                            "cap-rejects %llu cands-in-lambda %llu max %llu\n",
+                            (unsigned long long)tau.prim, tau.idx, hc[0], nfq, ndg, hc[1], dg[1],
+                            dg[2], dg[3]);
+                }
                 for (int it = 0; it < 100000 && npairs > 0; it++) {
                     CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
                     CK(launch_pair_fix(pairs, d + 5, npairs, pair_cap, inP, rej, d + 6, g->st));
@@ -879,11 +906,16 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         if (g->trace) {
             int dbg[4] = {0, 0, 0, 0};
             cudaMemcpy(dbg, d + 4, sizeof(dbg), cudaMemcpyDeviceToHost);
-            fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu\n",
-                    g->stats.rounds, (long long)live, (long long)need, dbg[0], removed);
+            fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu band %.3g\n",
+                    g->stats.rounds, (long long)live, (long long)need, dbg[0], removed, band);
         }
         live -= (int64_t)removed;
         if (live <= m) break;
+        if (!g->density_k1) {
+            double yield = ncand_a > 0 ? (double)removed / ncand_a : 1.0;
+            if (cap_over > 0 || yield < 0.5) band = std::max(band * 0.5, 1e-7);
+            else if (yield > 0.8) band = std::min(band * 1.25, band_max);
+        }
         // re-search the points whose stored neighbours were removed
         CK(launch_dirty(g->alive, g->nbr, g->ng, S, g->density_k1 ? S : k, dirty, g->st));
         CK(stable_compact(dirty, g->ng, list, d + 7, s, g->st));

@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
     danger_kernel(GridView g, const int* __restrict__ src, const int* __restrict__ nsrc,
                   const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
                   const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
-                  int k, int2* pairs, int* npairs, int pair_cap, int* overflow) {
+                  int k, int2* pairs, int* npairs, int pair_cap, int* overflow,
+                  unsigned long long* diag) {
     __shared__ int c_j[DG_WARPS][DG_CAP];
     __shared__ u64 c_d[DG_WARPS][DG_CAP];
     __shared__ int4 st_p[DG_WARPS][32];
@@ -396,6 +397,11 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
             }
             nc += __popc(bal);
         }
+    }
+    if (diag && lane == 0) {
+        if (nc > DG_CAP) atomicAdd(&diag[1], (unsigned long long)(nc - DG_CAP));
+        atomicAdd(&diag[2], (unsigned long long)nc);
+        atomicMax(&diag[3], (unsigned long long)nc);
     }
     nc = min(nc, DG_CAP);
     __syncwarp();
@@ -643,11 +649,11 @@ cudaError_t launch_kk_accept(const int* list, const int* nlist, int max_list, co
 cudaError_t launch_danger(const GridView& g, const int* src, const int* nsrc, int max_src,
                           const u64* prim, const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                           const u64* lam, int k, int2* pairs, int* npairs, int pair_cap,
-                          int* overflow, cudaStream_t st) {
+                          int* overflow, unsigned long long* diag, cudaStream_t st) {
     if (max_src <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((max_src + DG_WARPS - 1) / DG_WARPS);
     danger_kernel<<<blocks, DG_WARPS * 32, 0, st>>>(g, src, nsrc, prim, alive, inP, rej, lam, k,
-                                                    pairs, npairs, pair_cap, overflow); note_launch();
+                                                    pairs, npairs, pair_cap, overflow, diag); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_accept_above(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
