@@ -196,6 +196,15 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         g.free()
         return keep, st
 
+    if args.knn_only:
+        for _ in range(max(1, args.steps)):
+            g = pd.Grid(ctx, xyz_dev, stream=stream)
+            pd.pd_knn_cost(g, k=k, stream=stream)
+            g.free()
+        torch.cuda.synchronize()
+        print(json.dumps({"knn_only": True, "n": n, "k": k}))
+        return
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -226,15 +235,19 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
     value = units / tot_s
 
     # e2e: the host C-ABI entry with pinned buffers, copies inside the timed region
-    xyz_pin = torch.from_numpy(scan.xyz).pin_memory()
-    keep_pin = torch.empty(n, dtype=torch.uint8).pin_memory()
-    xyz_np, keep_np = xyz_pin.numpy(), keep_pin.numpy()
-    pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)   # warm
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)
-    e2e_s, e2e_units = aggregate(time.perf_counter() - t0, n * args.steps, dist)
+    e2e = None
+    if not args.no_e2e:
+        xyz_pin = torch.from_numpy(scan.xyz).pin_memory()
+        keep_pin = torch.empty(n, dtype=torch.uint8).pin_memory()
+        xyz_np, keep_np = xyz_pin.numpy(), keep_pin.numpy()
+        pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)
+        e2e_s, e2e_units = aggregate(time.perf_counter() - t0, n * args.steps, dist)
+        e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
+               "d2h_bytes_per_step": n}
 
     # roofline of the first full kNN/cost pass (one launch per step): algorithmic
     # bytes = per query 16 B read ({x,y,z,index}) + written key 8 + k-th d^2 8 +
@@ -270,8 +283,7 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
             "config": {"workload": wl["desc"], "n": n, "m": m, "k": k,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2"},
-            "e2e": {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
-                    "d2h_bytes_per_step": n},
+            "e2e": e2e,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
             "detail": {"rounds": mean["rounds"], "ms_knn": mean["ms_knn"],
@@ -291,6 +303,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="outdoor", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--knn-only", action="store_true",
+                    help="profiling aid: build the grid and run one full kNN/cost pass")
     args = ap.parse_args(argv)
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -81,7 +81,7 @@ typedef struct {
     double weight;            /* weight of the colour / orientation term */
     const float* normals_dev; /* n x 3 float32, input order (PD_TERM_ORIENT) */
     double band;              /* k >= 2: fraction of live points examined per
-                                 removal round (0 = default 0.2); never
+                                 removal round (0 = default 0.02); never
                                  changes the result */
     int32_t reserved[6];
 } pd_cost_params;

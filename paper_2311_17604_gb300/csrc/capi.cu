@@ -114,6 +114,7 @@ struct pd_grid {
     int* nbr;
     u64* rk2;
     uint8_t* flg;
+    u64* hz;  // k+b buffer horizon
     // small device scalars
     int* d_int;                  // [0] ngroups, [1..7] counters
     unsigned long long* d_u64;   // [0] counts
@@ -184,9 +185,8 @@ void gfree(pd_grid* g, void* p) { ctx_free(g->ctx, p, g->st); }
 
 // S = stored neighbours per point for a cost with k neighbours
 int width_for(int k, int density_k1) {
-    if (density_k1) return 8;
-    if (k + 1 <= 4) return 4;
-    if (k + 1 <= 8) return 8;
+    if (density_k1) return 8;  // the nearest-distance shell
+    if (k <= 6) return 8;      // k nearest + at least 2 spare (k+b buffer)
     return 17;
 }
 int filt_width(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 17); }
@@ -255,7 +255,7 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 // ============================================================ API: grid
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
-                    g->prim, g->nbr, g->rk2, g->flg, g->d_int, g->d_u64};
+                    g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -383,6 +383,7 @@ int prepare_state(pd_grid* g, const pd_cost_params* cp) {
     if (!g->nbr) ALLOC(g->nbr, int, (size_t)g->n * S);
     if (!g->rk2) ALLOC(g->rk2, u64, g->n);
     if (!g->flg) ALLOC(g->flg, uint8_t, g->n);
+    if (!g->hz) ALLOC(g->hz, u64, g->n);
     if (cp->term == PD_TERM_ORIENT) {
         if (!g->nrm) ALLOC(g->nrm, float4, g->n);
         // normals are given in input order: gather through pos[].w
@@ -409,6 +410,7 @@ KnnArgs base_args(pd_grid* g, const pd_cost_params* cp) {
     a.prim_out = g->prim;
     a.rk2_out = g->rk2;
     a.flg_out = g->flg;
+    a.hz_out = g->hz;
     return a;
 }
 
@@ -456,33 +458,6 @@ int knn_all(pd_grid* g, const pd_cost_params* cp, double* cost_s) {
     KnnArgs a = base_args(g, cp);
     a.cost_out = cost_s;
     CK(launch_knn(view_of(g), a, g->st));
-    return PD_OK;
-}
-
-// kNN over an ordered list of Morton positions (len on host)
-int knn_list(pd_grid* g, const pd_cost_params* cp, const int* list, int len, int filter,
-             int S, u64 tp, int ti, u64* fout) {
-    if (len <= 0) return PD_OK;
-    Scratch s = scratch_of(g);
-    int4* groups;
-    ALLOC(groups, int4, len);
-    int* d_ng = g->d_int + 1;
-    CK(launch_list_groups(view_of(g), list, len, groups, d_ng, s, g->st));
-    int ngr = 0;
-    CK(cudaMemcpyAsync(&ngr, d_ng, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-    CK(cudaStreamSynchronize(g->st));
-    KnnArgs a = base_args(g, cp);
-    a.groups = groups;
-    a.ngroups = ngr;
-    a.list = list;
-    a.filter = filter;
-    a.S = S;
-    a.tau_prim = tp;
-    a.tau_idx = ti;
-    if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
-    if (filter == FILT_BELOW_TAU) a.lam_out = fout;
-    CK(launch_knn(view_of(g), a, g->st));
-    gfree(g, groups);
     return PD_OK;
 }
 
@@ -541,6 +516,11 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
         CK(launch_take_u8(list, nl, g->flg, f2, g->st));
         gfree(g, g->flg);
         g->flg = f2;
+        u64* h2;
+        ALLOC(h2, u64, g->n);
+        CK(launch_take_u64(list, nl, g->hz, h2, g->st));
+        gfree(g, g->hz);
+        g->hz = h2;
         int* nb2;
         ALLOC(nb2, int, (size_t)g->n * g->S);
         CK(launch_remap(list, nl, g->nbr, nb2, newpos, g->ng, g->S, g->st));
@@ -645,6 +625,76 @@ int select_rank(pd_grid* g, const u64* prim, const uint8_t* alive, int64_t r, in
 }
 
 
+BufView bufview(pd_grid* g, const pd_cost_params* cp) {
+    BufView b;
+    b.pos = g->pos;
+    b.prim = g->prim;
+    b.nbr = g->nbr;
+    b.rk2 = g->rk2;
+    b.flg = g->flg;
+    b.hz = g->hz;
+    b.rgb = g->rgb;
+    b.nrm = g->nrm;
+    b.term = cp->term;
+    b.weight = cp->weight;
+    return b;
+}
+
+// kNN over the leaf groups, querying only the points whose flag is set.
+int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint8_t* qflag,
+             u64* fout, const RoundDev* rd) {
+    KnnArgs a = base_args(g, cp);
+    a.filter = filter;
+    a.S = S;
+    a.qflag = qflag;
+    a.rd = rd;
+    if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
+    if (filter == FILT_BELOW_TAU) a.lam_out = fout;
+    CK(launch_knn(view_of(g), a, g->st));
+    return PD_OK;
+}
+
+// A round the device could not settle: the danger analysis overflowed (or
+// fewer than k low points exist), or the fixpoint needed more sweeps.
+int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint8_t* rej,
+                 int* cand, int2* pairs, int pair_cap, int64_t* removed) {
+    int* d = g->d_int;
+    if (h.overflow) {
+        // drop this round's candidates and remove the global maximum only
+        CK(launch_remove(cand, &rd->ncand, 0, inP, rej, g->alive, g->d_u64, g->st));
+        CK(cudaMemsetAsync(inP, 0, g->ng, g->st));
+        CK(cudaMemsetAsync(rej, 0, g->ng, g->st));
+        Sel top;
+        int rc = select_rank(g, g->prim, g->alive, 1, 0, &top, nullptr);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(d + 4, 0, sizeof(int), g->st));
+        CK(launch_accept_above(g->prim, g->pos, g->alive, g->ng, top.prim, top.idx, inP, cand,
+                               d + 4, g->st));
+        CK(launch_remove(cand, d + 4, 1, inP, rej, g->alive, g->d_u64, g->st));
+    } else {
+        // keep sweeping the fixpoint until nothing changes
+        for (int it = 0; it < 1000000; it++) {
+            CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
+            if (g->density_k1)
+                CK(launch_k1_fix(cand, &rd->ncand, h.ncand, g->pos, g->nbr, g->S, inP, rej,
+                                 d + 6, g->st));
+            else
+                CK(launch_pair_fix(pairs, &rd->npairs, std::min(h.npairs, pair_cap), pair_cap,
+                                   inP, rej, d + 6, g->st));
+            int ch = 0;
+            CK(cudaMemcpyAsync(&ch, d + 6, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+            CK(cudaStreamSynchronize(g->st));
+            if (!ch) break;
+        }
+        CK(launch_remove(cand, &rd->ncand, h.ncand, inP, rej, g->alive, g->d_u64, g->st));
+    }
+    unsigned long long r = 0;
+    CK(cudaMemcpyAsync(&r, g->d_u64, sizeof(r), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    *removed = (int64_t)r;
+    return PD_OK;
+}
+
 // Duplicate phase: coincident points beyond the smallest index of their
 // class are the first pops of the sequential greedy (their cost is +inf).
 int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
@@ -705,8 +755,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     // or its yield is poor (the band then covers whole dense regions with no
     // lower keys inside), grown again while yields stay high.  Any band gives
     // the same result; only the number of rounds changes.
-    double band_max = cp->band > 0 ? cp->band : 0.05;
-    double band = band_max;
+    double band_max = cp->band > 0 ? cp->band : 0.02;
     int64_t live = g->n;
     // ---- duplicate phase
     int64_t nd = 0;
@@ -727,39 +776,50 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.q_first = g->ng;
     int S = g->S;
     int Sf = filt_width(k);
-    uint8_t *inP, *rej, *dirty, *fqf, *dgf;
-    int *cand, *slow, *list, *fql, *dgl;
-    u64 *fprim, *lam;
-    int2* pairs;
+    int kchk = g->density_k1 ? S : k;
+    bool use_buf = !g->density_k1 && S <= 8;
+    uint8_t *inP, *rej, *dirty, *fqf = nullptr, *dgf = nullptr;  // dgf: lambda search flags
+    int *cand, *slow, *src = nullptr;
+    u64 *fprim = nullptr, *lam = nullptr;
+    int2* pairs = nullptr;
     int64_t cap = g->n;
     ALLOC(inP, uint8_t, cap);
     ALLOC(rej, uint8_t, cap);
     ALLOC(dirty, uint8_t, cap);
     ALLOC(cand, int, cap);
     ALLOC(slow, int, cap);
-    ALLOC(list, int, cap);
     CK(cudaMemsetAsync(inP, 0, cap, g->st));
     CK(cudaMemsetAsync(rej, 0, cap, g->st));
     int pair_cap = 0;
-    fqf = dgf = nullptr;
-    fql = dgl = nullptr;
-    fprim = lam = nullptr;
-    pairs = nullptr;
     if (!g->density_k1) {
         ALLOC(fqf, uint8_t, cap);
         ALLOC(dgf, uint8_t, cap);
-        ALLOC(fql, int, cap);
-        ALLOC(dgl, int, cap);
+        ALLOC(src, int, cap);
         ALLOC(fprim, u64, cap);
         ALLOC(lam, u64, cap);
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
         ALLOC(pairs, int2, pair_cap);
     }
-    int* d = g->d_int;  // [4] ncand [5] nslow [6] changed [7] misc
-    Scratch s = scratch_of(g);
+    SelBuffers sb;
+    ALLOC(sb.p[0], u64, cap);
+    ALLOC(sb.p[1], u64, cap);
+    ALLOC(sb.i[0], int, cap);
+    ALLOC(sb.i[1], int, cap);
+    ALLOC(sb.hist, uint32_t, 4096);
+    CK(cudaMemsetAsync(sb.hist, 0, 4096 * sizeof(uint32_t), g->st));
+    RoundDev* rd;
+    ALLOC(rd, RoundDev, 1);
+    RoundDev h;
+    memset(&h, 0, sizeof(h));
+    h.live = live;
+    h.m = m;
+    h.band = band_max;
+    h.band_max = band_max;
+    h.density_k1 = g->density_k1;
+    h.band_mode = getenv("PD_BAND_MODE") ? atoi(getenv("PD_BAND_MODE")) : 1;
+    CK(cudaMemcpyAsync(rd, &h, sizeof(h), cudaMemcpyHostToDevice, g->st));
     int64_t built = live;
     while (live > m) {
-        int64_t need = live - m;
         g->stats.rounds++;
         if (g->max_rounds && g->stats.rounds > g->max_rounds) {
             set_err(g->ctx, "pd_decimate: stopped after %s%lld rounds (PD_MAX_ROUNDS)", "",
@@ -770,164 +830,79 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             set_err(g->ctx, "pd_decimate: round limit reached%s (live = %lld)", "", live);
             return PD_EINTERNAL;
         }
-        // k = 1: every key >= K* (the need-th largest) is examined.  k >= 2:
-        // only the r largest keys, r = min(band * live, need / 4) <= need, so
-        // the threshold is >= K* (condition R2 holds) and at least three
-        // quarters of the points still to be removed stay below it, where
-        // they shield candidates from farther sources (small search radii).
-        int64_t rank = need;
-        if (!g->density_k1) {
-            int64_t band_rank = (int64_t)(band * (double)live);
-            rank = std::max<int64_t>(1, std::min<int64_t>(band_rank, (need + 3) / 4));
-        }
-        Sel tau;
-        rc = select_rank(g, g->prim, g->alive, rank, 0, &tau, nullptr);
-        if (rc) return rc;
-        int ncand_a = 0;
-        unsigned long long cap_over = 0;
-        CK(cudaMemsetAsync(d + 4, 0, 4 * sizeof(int), g->st));
-        int hc[4];
+        GridView v = view_of(g);
+        CK(round_launch_setup(rd, g->st));
+        CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
         if (g->density_k1) {
-            CK(launch_k1_cand(g->prim, g->pos, g->alive, g->nbr, g->flg, g->ng, S, tau.prim,
-                              tau.idx, inP, cand, d + 4, slow, d + 5, g->st));
-            CK(cudaMemcpyAsync(hc, d + 4, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
-            CK(cudaStreamSynchronize(g->st));
-            if (hc[1] > 0)
-                CK(launch_k1_slow(view_of(g), g->prim, g->alive, g->rk2, slow, d + 5, hc[1], inP,
-                                  cand, d + 4, g->st));
-            CK(cudaMemcpyAsync(hc, d + 4, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-            CK(cudaStreamSynchronize(g->st));
-            int ncand = hc[0];
-            for (int it = 0; it < 100000; it++) {
-                CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
-                CK(launch_k1_fix(cand, d + 4, ncand, g->pos, g->nbr, S, inP, rej, d + 6, g->st));
-                int ch = 0;
-                CK(cudaMemcpyAsync(&ch, d + 6, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-                CK(cudaStreamSynchronize(g->st));
-                if (!ch) break;
-            }
-            CK(launch_remove(cand, d + 4, ncand, inP, rej, g->alive, g->d_u64, g->st));
+            CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
+                               rej, cand, slow, g->st));
         } else {
-            for (int attempt = 0; attempt < 2; attempt++) {
-                if (attempt == 1) {
-                    // only the global maximum: always removable
-                    Sel top;
-                    rc = select_rank(g, g->prim, g->alive, 1, 0, &top, nullptr);
-                    if (rc) return rc;
-                    tau = top;
-                    CK(cudaMemsetAsync(d + 4, 0, 4 * sizeof(int), g->st));
-                }
-                if (attempt == 1) {
-                    CK(launch_accept_above(g->prim, g->pos, g->alive, g->ng, tau.prim, tau.idx,
-                                           inP, cand, d + 4, g->st));
-                    break;
-                }
-                CK(launch_kk_cand(g->prim, g->pos, g->alive, g->nbr, g->flg, g->ng, S, k,
-                                  tau.prim, tau.idx, inP, cand, d + 4, fqf, dgf, g->st));
-                // (A) by a search restricted to smaller keys
-                CK(stable_compact(fqf, g->ng, fql, d + 7, s, g->st));
-                int nfq = 0, ndg = 0;
-                CK(cudaMemcpyAsync(&nfq, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-                CK(cudaStreamSynchronize(g->st));
-                g->stats.filtered_queries += nfq;
-                {
-                    Span t(T, &g->stats.ms_knn);
-                    rc = knn_list(g, cp, fql, nfq, FILT_BELOW_SELF, Sf, 0, 0, fprim);
-                    if (rc) return rc;
-                }
-                CK(cudaMemcpyAsync(d + 7, &nfq, sizeof(int), cudaMemcpyHostToDevice, g->st));
-                CK(launch_kk_accept(fql, d + 7, nfq, g->prim, fprim, inP, cand, d + 4, g->st));
-                // (B) danger pairs from points above tau with band points nearby
-                CK(stable_compact(dgf, g->ng, dgl, d + 7, s, g->st));
-                CK(cudaMemcpyAsync(&ndg, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-                CK(cudaStreamSynchronize(g->st));
-                g->stats.danger_queries += ndg;
-                {
-                    Span t(T, &g->stats.ms_knn);
-                    rc = knn_list(g, cp, dgl, ndg, FILT_BELOW_TAU, Sf, tau.prim, tau.idx, lam);
-                    if (rc) return rc;
-                }
-                CK(cudaMemcpyAsync(d + 7, &ndg, sizeof(int), cudaMemcpyHostToDevice, g->st));
-                CK(cudaMemsetAsync(d + 5, 0, 2 * sizeof(int), g->st));  // npairs, overflow
-                CK(cudaMemsetAsync(g->d_u64, 0, 4 * sizeof(u64), g->st));
-                CK(launch_danger(view_of(g), dgl, d + 7, ndg, g->prim, g->alive, inP, rej, lam,
-                                 k, pairs, d + 5, pair_cap, d + 6, g->d_u64, g->st));
-                CK(cudaMemcpyAsync(hc, d + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, g->st));
-                CK(cudaStreamSynchronize(g->st));
-                if (hc[2]) {
-                    // pair overflow or too few low points: clear and take the global max only
-                    CK(launch_remove(cand, d + 4, 0, inP, rej, g->alive, g->d_u64, g->st));
-                    // clear inP for all current candidates
-                    CK(cudaMemsetAsync(inP, 0, cap, g->st));
-                    CK(cudaMemsetAsync(rej, 0, cap, g->st));
-                    continue;
-                }
-                int npairs = std::min(hc[1], pair_cap);
-                ncand_a = hc[0];
-                {
-                    unsigned long long dg[4];
-                    CK(cudaMemcpyAsync(dg, g->d_u64, sizeof(dg), cudaMemcpyDeviceToHost, g->st));
-                    CK(cudaStreamSynchronize(g->st));
-                    cap_over = dg[1];
-                    if (g->trace)
-                    fprintf(stderr, "pd   k>=2: tau %016llx:%d cand(A) %d fq %d sources %d pairs %d "
-                            "cap-rejects %llu cands-in-lambda %llu max %llu\n",
-                            (unsigned long long)tau.prim, tau.idx, hc[0], nfq, ndg, hc[1], dg[1],
-                            dg[2], dg[3]);
-                }
-                for (int it = 0; it < 100000 && npairs > 0; it++) {
-                    CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
-                    CK(launch_pair_fix(pairs, d + 5, npairs, pair_cap, inP, rej, d + 6, g->st));
-                    int ch = 0;
-                    CK(cudaMemcpyAsync(&ch, d + 6, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-                    CK(cudaStreamSynchronize(g->st));
-                    if (!ch) break;
-                }
-                break;
+            BufView bv = bufview(g, cp);
+            CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,
+                                     g->st));
+            {
+                Span t(T, &g->stats.ms_knn);
+                rc = knn_flag(g, cp, FILT_BELOW_SELF, Sf, fqf, fprim, rd);
+                if (rc) return rc;
             }
-            int ncand = 0;
-            CK(cudaMemcpyAsync(&ncand, d + 4, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-            CK(cudaStreamSynchronize(g->st));
-            CK(launch_remove(cand, d + 4, ncand, inP, rej, g->alive, g->d_u64, g->st));
+            CK(round_launch_kk_accept(fqf, g->prim, fprim, g->ng, rd, inP, cand, g->st));
+            {
+                Span t(T, &g->stats.ms_knn);
+                rc = knn_flag(g, cp, FILT_BELOW_TAU, Sf, dgf, lam, rd);
+                if (rc) return rc;
+            }
+            CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k, pairs,
+                                   pair_cap, rd, g->st));
+            CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
         }
-        unsigned long long removed = 0;
-        CK(cudaMemcpyAsync(&removed, g->d_u64, sizeof(removed), cudaMemcpyDeviceToHost, g->st));
-        CK(cudaStreamSynchronize(g->st));
-        if (removed == 0 || (int64_t)removed > need) {
-            int dbg[4] = {0, 0, 0, 0};
-            cudaMemcpy(dbg, d + 4, sizeof(dbg), cudaMemcpyDeviceToHost);
-            snprintf(g->ctx->err, sizeof(g->ctx->err),
-                     "pd_decimate: round %d removed %llu points (need %lld, live %lld, "
-                     "candidates %d, slow %d, tau %016llx:%d)",
-                     g->stats.rounds, removed, (long long)need, (long long)live, dbg[0], dbg[1],
-                     (unsigned long long)tau.prim, tau.idx);
-            return PD_EINTERNAL;
+        CK(round_launch_remove(cand, inP, rej, g->alive, rd, g->st));
+        if (use_buf) {
+            // absorb removals in the k+b buffers; search only where < k remain
+            CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
+        } else {
+            CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
         }
-        if (g->trace) {
-            int dbg[4] = {0, 0, 0, 0};
-            cudaMemcpy(dbg, d + 4, sizeof(dbg), cudaMemcpyDeviceToHost);
-            fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu band %.3g\n",
-                    g->stats.rounds, (long long)live, (long long)need, dbg[0], removed, band);
-        }
-        live -= (int64_t)removed;
-        if (live <= m) break;
-        if (!g->density_k1) {
-            double yield = ncand_a > 0 ? (double)removed / ncand_a : 1.0;
-            if (cap_over > 0 || yield < 0.5) band = std::max(band * 0.5, 1e-7);
-            else if (yield > 0.8) band = std::min(band * 1.25, band_max);
-        }
-        // re-search the points whose stored neighbours were removed
-        CK(launch_dirty(g->alive, g->nbr, g->ng, S, g->density_k1 ? S : k, dirty, g->st));
-        CK(stable_compact(dirty, g->ng, list, d + 7, s, g->st));
-        int nl = 0;
-        CK(cudaMemcpyAsync(&nl, d + 7, sizeof(int), cudaMemcpyDeviceToHost, g->st));
-        CK(cudaStreamSynchronize(g->st));
-        g->stats.requeries += nl;
         {
             Span t(T, &g->stats.ms_knn_requery);
-            rc = knn_list(g, cp, list, nl, FILT_NONE, S, 0, 0, nullptr);
+            rc = knn_flag(g, cp, FILT_NONE, S, dirty, nullptr, rd);
             if (rc) return rc;
         }
+        CK(round_launch_finish(rd, g->st));
+        CK(cudaMemcpyAsync(&h, rd, sizeof(h), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        if (h.overflow || h.fix_unconverged) {
+            // settle on the host: finish the fixpoint, or (danger overflow / too
+            // few low points) take only the global maximum, always removable
+            int64_t removed = 0;
+            rc = settle_round(g, rd, h, inP, rej, cand, pairs, pair_cap, &removed);
+            if (rc) return rc;
+            if (use_buf)
+                CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
+            else
+                CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
+            {
+                Span t(T, &g->stats.ms_knn_requery);
+                rc = knn_flag(g, cp, FILT_NONE, S, dirty, nullptr, rd);
+                if (rc) return rc;
+            }
+            h.live -= removed;
+            h.removed = (unsigned long long)removed;
+            CK(cudaMemcpyAsync(&rd->live, &h.live, sizeof(h.live), cudaMemcpyHostToDevice,
+                               g->st));
+            CK(cudaMemcpyAsync(&rd->tot_requery, &h.tot_requery, sizeof(u64),
+                               cudaMemcpyHostToDevice, g->st));
+        }
+        if (g->trace)
+            fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu band %.3g "
+                    "sources %d pairs %d cap-over %llu%s\n", g->stats.rounds, (long long)live,
+                    (long long)(live - m), h.ncand, h.removed, h.band, h.nsrc, h.npairs,
+                    h.cap_over, h.overflow ? " overflow" : (h.fix_unconverged ? " unconverged" : ""));
+        if (h.removed == 0 || (int64_t)h.removed > live - m) {
+            set_err(g->ctx, "pd_decimate: round removed %s%lld points", "", (long long)h.removed);
+            return PD_EINTERNAL;
+        }
+        live = h.live;
+        if (live <= m) break;
         // every live point now stores live neighbours only: safe to compact
         if (live * 2 < built) {
             Span t(T, &g->stats.ms_build);
@@ -936,9 +911,13 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             built = live;
         }
     }
+    g->stats.requeries = (int64_t)h.tot_requery;
+    g->stats.filtered_queries = (int64_t)h.tot_filtered;
+    g->stats.danger_queries = (int64_t)h.tot_lambda;
     CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
     CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
-    void* fr[] = {inP, rej, dirty, cand, slow, list, fqf, dgf, fql, dgl, fprim, lam, pairs};
+    void* fr[] = {inP, rej, dirty, cand, slow, src, fqf, dgf, fprim, lam, pairs,
+                  sb.p[0], sb.p[1], sb.i[0], sb.i[1], sb.hist, rd};
     for (void* p : fr) gfree(g, p);
     cudaEventRecord(e1, g->st);
     CK(cudaEventSynchronize(e1));

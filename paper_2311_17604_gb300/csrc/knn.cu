@@ -190,7 +190,11 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
     int cnt = G.y;
     int L = G.z;
     int q = -1;
-    if (lane < cnt) q = a.list ? a.list[G.x + lane] : G.x + lane;
+    if (lane < cnt) {
+        q = a.list ? a.list[G.x + lane] : G.x + lane;
+        if (a.qflag && !a.qflag[q]) q = -1;
+    }
+    if (!__any_sync(FULLM, q >= 0)) return;
     int q0 = a.list ? a.list[G.x] : G.x;
     u64 c0 = g.code[q0];
     int4 qp = q >= 0 ? g.pos[q] : make_int4(0, 0, 0, 0);
@@ -201,11 +205,14 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
         tp = a.prim[q];
         ti = qp.w;
     } else if (FILT == FILT_BELOW_TAU) {
-        tp = a.tau_prim;
-        ti = a.tau_idx;
+        tp = a.rd ? a.rd->tau_prim : a.tau_prim;
+        ti = a.rd ? a.rd->tau_idx : a.tau_idx;
     }
     // exactness bound: the R-th smallest distance must be exact
-    const int R = (FILT == FILT_NONE && a.density_k1) ? 1 : a.k;
+    // k = 1 density: the nearest distance and its complete shell; other full
+    // searches: all S stored neighbours exact (the k+b neighbour buffer, so a
+    // removal can be absorbed without a new search); filtered searches: k.
+    const int R = FILT == FILT_NONE ? (a.density_k1 ? 1 : S) : a.k;
     TopList<S> top;
     top.init();
     bool todo = q >= 0;
@@ -284,6 +291,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
                         a.rk2_out[q] = dk;
                         bool tie = found > k && top.at(k) == dk;
                         a.flg_out[q] = (uint8_t)(tie ? 1 : 0);
+                        if (a.hz_out) a.hz_out[q] = top.d[S - 1];
                         if (a.cost_out) a.cost_out[q] = c;
                     }
                 } else if (FILT == FILT_BELOW_SELF) {

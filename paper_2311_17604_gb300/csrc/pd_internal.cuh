@@ -134,6 +134,39 @@ __device__ inline bool key_gt(unsigned long long pa, int ia, unsigned long long 
     return pa > pb || (pa == pb && ia > ib);
 }
 
+// Per-neighbour weight of the optional cost terms (section "Additional cost
+// terms"): 1 - a * ||rgb_p - rgb_q|| / (255 sqrt 3) for colour, 1 - a * (1 -
+// |n_p . n_q|) for orientation (Eq. 13), 1 otherwise.  Every operation is a
+// separately rounded binary64 operation (no contraction).
+__device__ inline double term_weight(int term, double a, const uchar4* rgb, const float4* nrm,
+                                     int q, int j) {
+    if (term == 1) {
+        uchar4 p = rgb[q], r = rgb[j];
+        double dr = (double)p.x - (double)r.x;
+        double dg = (double)p.y - (double)r.y;
+        double db = (double)p.z - (double)r.z;
+        double s = __dmul_rn(dr, dr);
+        s = __dadd_rn(s, __dmul_rn(dg, dg));
+        s = __dadd_rn(s, __dmul_rn(db, db));
+        double dist = __dsqrt_rn(s);
+        double scale = __dmul_rn(255.0, __dsqrt_rn(3.0));
+        return __dsub_rn(1.0, __dmul_rn(a, __ddiv_rn(dist, scale)));
+    }
+    if (term == 2) {
+        float4 p = nrm[q], r = nrm[j];
+        double d = __dmul_rn((double)p.x, (double)r.x);
+        d = __dadd_rn(d, __dmul_rn((double)p.y, (double)r.y));
+        d = __dadd_rn(d, __dmul_rn((double)p.z, (double)r.z));
+        return __dsub_rn(1.0, __dmul_rn(a, __dsub_rn(1.0, fabs(d))));
+    }
+    return 1.0;
+}
+
+__device__ inline unsigned long long sqd(int4 a, int4 b) {
+    long long dx = (long long)a.x - b.x, dy = (long long)a.y - b.y, dz = (long long)a.z - b.z;
+    return (unsigned long long)(dx * dx + dy * dy + dz * dz);
+}
+
 // ---------------------------------------------------------------- launches
 // Number of kernels this library has launched (process-wide, host counter).
 extern long long g_launch_count;

@@ -50,6 +50,33 @@ cudaError_t launch_list_groups(const GridView& g, const int* list, int64_t len, 
 cudaError_t stable_compact(const uint8_t* flag, int64_t n, int* out, int* count,
                            const Scratch& s, cudaStream_t st);
 
+// ---------------------------------------------------------------- round state
+#define PD_FIX_ITERS 8
+
+// Per-round control block in device memory (read by the host once per round).
+struct RoundDev {
+    long long live, m, need, rank;
+    double band, band_max;
+    unsigned long long removed, cap_over;
+    unsigned long long tot_requery, tot_filtered, tot_sources, tot_updated, tot_lambda;
+    unsigned long long tau_prim;
+    int tau_idx;
+    int done;
+    unsigned pre[8];
+    int len[2];
+    int ncand, nslow, nsrc, npairs, overflow;
+    int changed[PD_FIX_ITERS];
+    int fix_unconverged;
+    int density_k1;
+    int band_mode;  // 0: shrink on overflow only; 1: also on poor yield
+};
+
+struct SelBuffers {
+    u64* p[2];
+    int* i[2];
+    uint32_t* hist;
+};
+
 // ---------------------------------------------------------------- knn.cu
 enum { FILT_NONE = 0, FILT_BELOW_SELF = 1, FILT_BELOW_TAU = 2 };
 
@@ -62,6 +89,8 @@ struct KnnArgs {
     int filter;
     u64 tau_prim;
     int tau_idx;
+    const RoundDev* rd;       // when set, tau is read from rd (device)
+    const uint8_t* qflag;     // when set, only flagged points of each group are queried
     int k;
     int S;                    // stored neighbours (template width)
     int density_k1;           // integer-ordered k = 1 density cost
@@ -74,6 +103,7 @@ struct KnnArgs {
     u64* prim_out;            // key primary
     u64* rk2_out;             // k-th squared distance
     uint8_t* flg_out;
+    u64* hz_out;              // horizon: S-th stored squared distance (~0 if fewer)
     double* cost_out;         // cost in Morton order (optional)
     // outputs (filter modes)
     u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
@@ -87,4 +117,50 @@ struct SelectResult {
     int idx;
 };
 
+}  // namespace pd
+
+namespace pd {
+// ---------------------------------------------------------------- rounds_dev.cu
+cudaError_t round_launch_setup(RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_finish(RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
+                                SelBuffers& b, RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
+                            const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
+                            RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
+                            cudaStream_t st);
+cudaError_t round_launch_kk_cand(const u64* prim, const int4* pos, const uint8_t* alive,
+                                 const int* nbr, const uint8_t* flg, int64_t n, int S, int k,
+                                 RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                 uint8_t* dg_flag, int* src, cudaStream_t st);
+cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
+                                   int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
+                                   cudaStream_t st);
+cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
+                                const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
+                                const u64* lam, const int* nbr, int S, int k, int2* pairs,
+                                int pair_cap, RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_pairs_fix(const int2* pairs, int pair_cap, const uint8_t* inP,
+                                   uint8_t* rej, RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_remove(const int* cand, uint8_t* inP, uint8_t* rej, uint8_t* alive,
+                                RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_dirty(const uint8_t* alive, const int* nbr, int64_t n, int S, int kchk,
+                               uint8_t* dirty, RoundDev* rd, cudaStream_t st);
+struct BufView {  // the k+b neighbour buffer of every point
+    const int4* pos;
+    u64* prim;
+    int* nbr;
+    u64* rk2;
+    uint8_t* flg;
+    u64* hz;
+    const uchar4* rgb;
+    const float4* nrm;
+    int term;
+    double weight;
+};
+cudaError_t round_launch_kk_update(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
+                                   uint8_t* dirty, RoundDev* rd, cudaStream_t st);
+cudaError_t round_launch_kk_cand2(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
+                                  RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                  uint8_t* lq_flag, u64* lam, int* src, cudaStream_t st);
 }  // namespace pd

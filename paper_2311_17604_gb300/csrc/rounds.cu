@@ -300,6 +300,20 @@ __global__ void kk_accept_kernel(const int* __restrict__ list, const int* __rest
 // could enter x's k nearest before it is popped: record (x, p).
 #define DG_CAP 512
 #define DG_WARPS 2
+#define PD_DG_SMAX 8  // stored neighbours used as shields (S up to 8)
+
+__device__ inline u64 box_d2x(int ux, int uy, int uz, int bx, int by, int bz, int sh) {
+    long long q[3] = {ux, uy, uz};
+    int c[3] = {bx, by, bz};
+    u64 s = 0;
+    for (int a = 0; a < 3; a++) {
+        long long lo = (long long)c[a] << sh;
+        long long hi = ((long long)(c[a] + 1) << sh) - 1;
+        long long d = q[a] < lo ? lo - q[a] : (q[a] > hi ? q[a] - hi : 0);
+        s += (u64)(d * d);
+    }
+    return s;
+}
 
 // Cells of the level-L cube around a point that hold every point closer than
 // sqrt(lam); returns the level (the first whose cube covers that ball).
@@ -334,21 +348,25 @@ __device__ inline int cover_level(const GridView& g, int ux, int uy, int uz, u64
 //      reach k; a count below k means p could enter x's k nearest before p is
 //      popped: record (x, p).
 // Candidates beyond the list capacity are rejected without counting.
-__global__ void __launch_bounds__(DG_WARPS * 32)
-    danger_kernel(GridView g, const int* __restrict__ src, const int* __restrict__ nsrc,
-                  const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
-                  const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
-                  int k, int2* pairs, int* npairs, int pair_cap, int* overflow,
-                  unsigned long long* diag) {
-    __shared__ int c_j[DG_WARPS][DG_CAP];
-    __shared__ u64 c_d[DG_WARPS][DG_CAP];
-    __shared__ int4 st_p[DG_WARPS][32];
-    __shared__ u64 st_k[DG_WARPS][32];
-    __shared__ int st_o[DG_WARPS][32];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int t = blockIdx.x * DG_WARPS + w;
-    if (t >= *nsrc) return;
-    int x = src[t];
+struct DangerSmem {
+    int c_j[DG_WARPS][DG_CAP];
+    u64 c_d[DG_WARPS][DG_CAP];
+    int4 st_p[DG_WARPS][32];
+    u64 st_k[DG_WARPS][32];
+    int st_o[DG_WARPS][32];
+};
+
+__device__ void danger_one(const GridView& g, int x, const u64* __restrict__ prim,
+                           const uint8_t* __restrict__ alive, const uint8_t* __restrict__ inP,
+                           uint8_t* rej, const u64* __restrict__ lam, const int* __restrict__ nbr,
+                           int S, int k, int2* pairs, int* npairs, int pair_cap, int* overflow,
+                           unsigned long long* diag, DangerSmem& sm, int w, int lane) {
+    int(&c_j)[DG_WARPS][DG_CAP] = sm.c_j;
+    u64(&c_d)[DG_WARPS][DG_CAP] = sm.c_d;
+    int4(&st_p)[DG_WARPS][32] = sm.st_p;
+    u64(&st_k)[DG_WARPS][32] = sm.st_k;
+    int(&st_o)[DG_WARPS][32] = sm.st_o;
+    __syncwarp();
     int4 xp = g.pos[x];
     u64 px = prim[x];
     u64 lx = lam[x];
@@ -368,6 +386,15 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
         uint32_t bj = __shfl_sync(FULLM, rb, j);
         int tj = __shfl_sync(FULLM, rt, j);
         if (j < lane && rt == 2 && tj == 2 && bj == rb) rt = 0;
+    }
+    // squared distance from x to each resolved range's box: ranges entirely
+    // beyond lam (or beyond the candidates being counted) are skipped
+    u64 rbox = ~0ull;
+    if (rt) {
+        int sh = rl - L;
+        rbox = box_d2x(ux, uy, uz, (cx + dx) >> sh, (cy + dy) >> sh, (cz + dz) >> sh,
+                       rl + g.shift);
+        if (rbox >= lx) rt = 0;
     }
     // 1. candidates
     int nc = 0;
@@ -399,12 +426,32 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
         }
     }
     if (diag && lane == 0) {
-        if (nc > DG_CAP) atomicAdd(&diag[1], (unsigned long long)(nc - DG_CAP));
-        atomicAdd(&diag[2], (unsigned long long)nc);
-        atomicMax(&diag[3], (unsigned long long)nc);
+        if (nc > DG_CAP) atomicAdd(diag, (unsigned long long)(nc - DG_CAP));
     }
     nc = min(nc, DG_CAP);
     __syncwarp();
+    // x's stored neighbours are live points near x: the cheapest shields
+    int sn_j[PD_DG_SMAX];
+    u64 sn_d[PD_DG_SMAX], sn_k[PD_DG_SMAX];
+    int sn_i[PD_DG_SMAX];
+#pragma unroll
+    for (int i = 0; i < PD_DG_SMAX; i++) {
+        sn_j[i] = -1;
+        sn_d[i] = ~0ull;
+        sn_k[i] = 0;
+        sn_i[i] = 0;
+        if (nbr && i < S && nc > 0) {
+            int y = nbr[(int64_t)x * S + i];
+            if (y >= 0) {
+                int4 v = g.pos[y];
+                long long ddx = v.x - xp.x, ddy = v.y - xp.y, ddz = v.z - xp.z;
+                sn_j[i] = y;
+                sn_d[i] = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
+                sn_k[i] = prim[y];
+                sn_i[i] = v.w;
+            }
+        }
+    }
     // 2. counting, 32 candidates at a time
     for (int a0 = 0; a0 < nc; a0 += 32) {
         int a = a0 + lane;
@@ -414,10 +461,25 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
         u64 pp = done ? 0 : prim[p];
         int ip = done ? 0 : g.pos[p].w;
         int cnt = 0;
+        if (!done) {
+#pragma unroll
+            for (int i = 0; i < PD_DG_SMAX; i++)
+                if (sn_j[i] >= 0 && sn_j[i] != p && sn_d[i] <= dp &&
+                    key_gt(pp, ip, sn_k[i], sn_i[i]))
+                    cnt++;
+            if (cnt >= k) done = true;
+            cnt = 0;  // the stream below recounts every point (stored ones included)
+        }
+        u64 dmax = done ? 0 : dp;  // farthest candidate of this batch
+        for (int o2 = 16; o2; o2 >>= 1) {
+            u64 other = __shfl_xor_sync(FULLM, dmax, o2);
+            dmax = other > dmax ? other : dmax;
+        }
         for (int r = 0; r < 27; r++) {
             int tr = __shfl_sync(FULLM, rt, r);
             if (!tr) continue;
             if (__all_sync(FULLM, done)) break;
+            if (__shfl_sync(FULLM, rbox, r) > dmax) continue;
             uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
             for (uint32_t c = b; c < e; c += 32) {
                 uint32_t j = c + lane;
@@ -455,6 +517,20 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
             else *overflow = 1;
         }
     }
+}
+
+__global__ void __launch_bounds__(DG_WARPS * 32)
+    danger_kernel(GridView g, const int* __restrict__ src, const int* __restrict__ nsrc,
+                  const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
+                  const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
+                  const int* __restrict__ nbr, int S, int k, int2* pairs, int* npairs,
+                  int pair_cap, int* overflow, unsigned long long* diag) {
+    __shared__ DangerSmem sm;
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ns = *nsrc;
+    for (int t = blockIdx.x * DG_WARPS + w; t < ns; t += gridDim.x * DG_WARPS)
+        danger_one(g, src[t], prim, alive, inP, rej, lam, nbr, S, k, pairs, npairs, pair_cap,
+                   overflow, diag, sm, w, lane);
 }
 
 // Fallback: accept every live point with key >= tau (tau = the top key).
@@ -652,8 +728,19 @@ cudaError_t launch_danger(const GridView& g, const int* src, const int* nsrc, in
                           int* overflow, unsigned long long* diag, cudaStream_t st) {
     if (max_src <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((max_src + DG_WARPS - 1) / DG_WARPS);
-    danger_kernel<<<blocks, DG_WARPS * 32, 0, st>>>(g, src, nsrc, prim, alive, inP, rej, lam, k,
-                                                    pairs, npairs, pair_cap, overflow, diag); note_launch();
+    danger_kernel<<<blocks, DG_WARPS * 32, 0, st>>>(g, src, nsrc, prim, alive, inP, rej, lam,
+                                                    nullptr, 0, k, pairs, npairs, pair_cap,
+                                                    overflow, diag); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
+                                const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
+                                const u64* lam, const int* nbr, int S, int k, int2* pairs,
+                                int pair_cap, RoundDev* rd, cudaStream_t st) {
+    danger_kernel<<<152 * 4, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
+                                                     lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
+                                                     pairs, &rd->npairs, pair_cap, &rd->overflow,
+                                                     &rd->cap_over); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_accept_above(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,

@@ -1,0 +1,661 @@
+// rounds_dev.cu -- removal rounds driven from device memory.
+//
+// One round is a fixed sequence of launches whose sizes never depend on
+// counts computed in the round: the threshold tau comes from an on-device
+// radix select, candidate / source / pair lists are appended with atomics and
+// walked by grid-stride or persistent kernels, neighbour searches run over
+// the leaf groups with a per-point flag, and the fixpoint runs a fixed number
+// of sweeps.  The host reads the small RoundDev block once per round.
+// The rules themselves (R2, A, B) are documented in rounds.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+namespace pd {
+
+#define FULLM 0xffffffffu
+#define PERSIST_BLOCKS (152 * 8)
+
+// ------------------------------------------------------------------ setup
+__global__ void round_setup_kernel(RoundDev* rd) {
+    if (threadIdx.x != 0) return;
+    long long need = rd->live - rd->m;
+    rd->need = need;
+    long long rank = need;
+    if (!rd->density_k1) {
+        long long band_rank = (long long)(rd->band * (double)rd->live);
+        long long quarter = (need + 3) / 4;
+        rank = band_rank < quarter ? band_rank : quarter;
+        if (rank < 1) rank = 1;
+    }
+    rd->rank = rank;
+    rd->done = 0;
+    rd->len[0] = rd->len[1] = 0;
+    rd->ncand = rd->nslow = rd->nsrc = rd->npairs = rd->overflow = 0;
+    rd->removed = 0;
+    rd->cap_over = 0;
+    rd->fix_unconverged = 0;
+    for (int i = 0; i < PD_FIX_ITERS; i++) rd->changed[i] = 0;
+}
+
+__global__ void round_finish_kernel(RoundDev* rd) {
+    if (threadIdx.x != 0) return;
+    rd->live -= (long long)rd->removed;
+    rd->tot_sources += (unsigned long long)rd->nsrc;
+    if (!rd->density_k1) {
+        bool shrink = rd->cap_over != 0;
+        double grow = 1.5;
+        if (rd->band_mode == 1) {
+            double yield = rd->ncand > 0 ? (double)rd->removed / rd->ncand : 1.0;
+            shrink = shrink || yield < 0.5;
+            grow = yield > 0.8 ? 1.25 : 1.0;
+        }
+        double b = shrink ? rd->band * 0.5 : rd->band * grow;
+        if (b > rd->band_max) b = rd->band_max;
+        if (b < 1e-7) b = 1e-7;
+        rd->band = b;
+    }
+}
+
+// ------------------------------------------------------------------ selection
+__device__ inline uint32_t sel_digit(u64 prim, int idx, int pass) {
+    int lo = 84 - 12 * pass;
+    uint32_t ui = (uint32_t)idx;
+    if (lo >= 32) return (uint32_t)(prim >> (lo - 32)) & 0xfffu;
+    if (lo + 12 <= 32) return (ui >> lo) & 0xfffu;
+    int nlow = 32 - lo;
+    return ((uint32_t)(prim << nlow) | (ui >> lo)) & 0xfffu;
+}
+
+// pass 0 reads every alive grid point; pass p > 0 reads the list compacted by
+// pass p-1 (buffer (p-1)&1).
+__global__ void seld_hist_kernel(const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
+                                 int64_t n, const u64* __restrict__ bp0, const int* __restrict__ bi0,
+                                 const u64* __restrict__ bp1, const int* __restrict__ bi1,
+                                 int pass, const RoundDev* rd, uint32_t* hist) {
+    if (rd->done) return;
+    __shared__ uint32_t h[4096];
+    for (int x = threadIdx.x; x < 4096; x += blockDim.x) h[x] = 0;
+    __syncthreads();
+    const u64* lp = ((pass - 1) & 1) ? bp1 : bp0;
+    const int* li = ((pass - 1) & 1) ? bi1 : bi0;
+    int64_t len = pass ? (int64_t)rd->len[(pass - 1) & 1] : n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (pass) {
+            atomicAdd(&h[sel_digit(lp[i], li[i], pass)], 1u);
+        } else {
+            if (!alive[i]) continue;
+            atomicAdd(&h[(uint32_t)(prim[i] >> 52)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < 4096; x += blockDim.x)
+        if (h[x]) atomicAdd(&hist[x], h[x]);
+}
+
+// One block of 256 threads: find the bin holding rank rd->rank (counted from
+// the largest key), record the digit, and finish when the bin boundary is the
+// exact threshold.  Clears the histogram for the next pass.
+__global__ void seld_find_kernel(uint32_t* hist, int pass, RoundDev* rd) {
+    __shared__ unsigned long long part[256];
+    __shared__ int found_bin;
+    __shared__ unsigned long long found_cum;
+    if (rd->done) {
+        for (int x = threadIdx.x; x < 4096; x += blockDim.x) hist[x] = 0;
+        return;
+    }
+    int t = threadIdx.x;
+    // thread t owns bins [4095 - 16t - 15, 4095 - 16t] (descending)
+    unsigned long long s = 0;
+    for (int j = 0; j < 16; j++) s += hist[4095 - 16 * t - j];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {  // inclusive scan over threads
+        unsigned long long v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned long long before = t ? part[t - 1] : 0;
+    long long r = rd->rank;
+    if (t == 0) found_bin = -1;
+    __syncthreads();
+    if ((long long)before < r && (long long)part[t] >= r) {
+        unsigned long long c = before;
+        for (int j = 0; j < 16; j++) {
+            int b = 4095 - 16 * t - j;
+            if ((long long)(c + hist[b]) >= r) {
+                found_bin = b;
+                found_cum = c;
+                break;
+            }
+            c += hist[b];
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        int b = found_bin;
+        if (b < 0) {  // rank beyond the live count: cannot happen; stop selecting
+            rd->done = 1;
+            rd->overflow = 1;
+        } else {
+            rd->pre[pass] = (unsigned)b;
+            unsigned long long hb = hist[b];
+            bool exact = (long long)(found_cum + hb) == r || pass == 7;
+            rd->rank = r - (long long)found_cum;
+            if (exact) {
+                unsigned __int128 v = 0;
+                for (int p = 0; p < 8; p++) {
+                    v <<= 12;
+                    if (p <= pass) v |= rd->pre[p];
+                }
+                rd->tau_prim = (unsigned long long)(v >> 32);
+                rd->tau_idx = (int)(uint32_t)v;
+                rd->done = 1;
+            }
+            rd->len[pass & 1] = 0;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < 4096; x += blockDim.x) hist[x] = 0;
+}
+
+__global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
+                                    const uint8_t* __restrict__ alive, int64_t n, u64* bp0, int* bi0,
+                                    u64* bp1, int* bi1, int pass, RoundDev* rd) {
+    if (rd->done) return;
+    const u64* lp = ((pass - 1) & 1) ? bp1 : bp0;
+    const int* li = ((pass - 1) & 1) ? bi1 : bi0;
+    u64* op = (pass & 1) ? bp1 : bp0;
+    int* oi = (pass & 1) ? bi1 : bi0;
+    int64_t len = pass ? (int64_t)rd->len[(pass - 1) & 1] : n;
+    uint32_t want = rd->pre[pass];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        u64 p;
+        int id;
+        if (pass) {
+            p = lp[i];
+            id = li[i];
+            if (sel_digit(p, id, pass) != want) continue;
+        } else {
+            if (!alive[i]) continue;
+            p = prim[i];
+            if ((uint32_t)(p >> 52) != want) continue;
+            id = pos[i].w;
+        }
+        int slot = atomicAdd(&rd->len[pass & 1], 1);
+        op[slot] = p;
+        oi[slot] = id;
+    }
+}
+
+// ------------------------------------------------------------------ k = 1
+__global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
+                                const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
+                                const uint8_t* __restrict__ flg, int64_t n, int S, RoundDev* rd,
+                                uint8_t* inP, int* cand, int* slow) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n || !alive[s]) return;
+    u64 ps = prim[s];
+    int is = pos[s].w;
+    if (key_gt(rd->tau_prim, rd->tau_idx, ps, is)) return;
+    if (flg[s] & 2) {
+        slow[atomicAdd(&rd->nslow, 1)] = (int)s;
+        return;
+    }
+    bool ok = nbr[s * S] < 0;
+    for (int i = 0; i < S && !ok; i++) {
+        int x = nbr[s * S + i];
+        if (x < 0) continue;
+        if (key_gt(ps, is, prim[x], pos[x].w)) ok = true;
+    }
+    if (ok) {
+        inP[s] = 1;
+        cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+    }
+}
+
+// overflowing shells: accept iff every live point at distance d1 has a
+// smaller key (grid-stride over the slow list)
+__global__ void k1d_slow_kernel(GridView g, const u64* __restrict__ prim,
+                                const uint8_t* __restrict__ alive, const u64* __restrict__ rk2,
+                                const int* __restrict__ slow, RoundDev* rd, uint8_t* inP,
+                                int* cand) {
+    int ns = rd->nslow;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += gridDim.x * blockDim.x) {
+        int s = slow[t];
+        int4 qp = g.pos[s];
+        u64 r2 = rk2[s];
+        u64 ps = prim[s];
+        int ux = qp.x - g.origin.x, uy = qp.y - g.origin.y, uz = qp.z - g.origin.z;
+        u64 c0 = g.code[s];
+        bool ok = true;
+        for (int L = g.leaf[s]; L <= g.B; L++) {
+            int cx = 0, cy = 0, cz = 0;
+            if (L < g.B) {
+                cx = (int)compact3(c0 >> (3 * L));
+                cy = (int)compact3(c0 >> (3 * L + 1));
+                cz = (int)compact3(c0 >> (3 * L + 2));
+            }
+            int sh = L + g.shift;
+            long long q[3] = {ux, uy, uz};
+            int c[3] = {cx, cy, cz};
+            int m[3] = {g.umax.x, g.umax.y, g.umax.z};
+            long long best = -1;
+            for (int a = 0; a < 3; a++) {
+                long long lo = (long long)(c[a] - 1) << sh, hi = (long long)(c[a] + 2) << sh;
+                if (lo > 0 && (best < 0 || q[a] - lo + 1 < best)) best = q[a] - lo + 1;
+                if (hi <= m[a] && (best < 0 || hi - q[a] < best)) best = hi - q[a];
+            }
+            bool covered = L >= g.B || best < 0 || r2 < (u64)best * (u64)best;
+            if (!covered) continue;
+            for (int o = 0; o < 27 && ok; o++) {
+                int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                uint32_t b, e;
+                int lvl;
+                if (!resolve_cell(g, L, cx + dx, cy + dy, cz + dz, b, e, &lvl)) continue;
+                for (uint32_t j = b; j < e && ok; j++) {
+                    if ((int)j == s || !alive[j]) continue;
+                    int4 v = g.pos[j];
+                    long long dx2 = v.x - qp.x, dy2 = v.y - qp.y, dz2 = v.z - qp.z;
+                    u64 d2 = (u64)(dx2 * dx2 + dy2 * dy2 + dz2 * dz2);
+                    if (d2 == r2 && key_gt(prim[j], v.w, ps, qp.w)) ok = false;
+                }
+            }
+            break;
+        }
+        if (ok) {
+            inP[s] = 1;
+            cand[atomicAdd(&rd->ncand, 1)] = s;
+        }
+    }
+}
+
+__global__ void k1d_fix_kernel(const int* __restrict__ cand, const int4* __restrict__ pos,
+                               const int* __restrict__ nbr, int S, const uint8_t* __restrict__ inP,
+                               uint8_t* rej, int iter, RoundDev* rd) {
+    if (iter > 0 && !rd->changed[iter - 1]) return;
+    int nc = rd->ncand;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+        int s = cand[t];
+        if (rej[s]) continue;
+        int is = pos[s].w;
+        for (int i = 0; i < S; i++) {
+            int x = nbr[(int64_t)s * S + i];
+            if (x < 0) continue;
+            if (pos[x].w > is && (!inP[x] || rej[x])) {
+                rej[s] = 1;
+                rd->changed[iter] = 1;
+                break;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k >= 2
+__global__ void kkd_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
+                                const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
+                                const uint8_t* __restrict__ flg, int64_t n, int S, int k,
+                                RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                uint8_t* dg_flag, int* src) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool fq = false;
+    if (s < n) {
+        uint8_t dgv = 0;
+        if (alive[s]) {
+            u64 tp = rd->tau_prim;
+            int ti = rd->tau_idx;
+            u64 ps = prim[s];
+            int is = pos[s].w;
+            if (!key_gt(tp, ti, ps, is)) {
+                bool lower = !(flg[s] & 1);
+                bool band_nbr = (flg[s] & 1) != 0 || nbr[s * S + k - 1] < 0;
+                for (int i = 0; i < k; i++) {
+                    int x = nbr[s * S + i];
+                    if (x < 0) continue;
+                    u64 px = prim[x];
+                    int ix = pos[x].w;
+                    if (key_gt(px, ix, ps, is)) lower = false;
+                    if (!key_gt(tp, ti, px, ix)) band_nbr = true;
+                }
+                if (lower) {
+                    inP[s] = 1;
+                    cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+                } else {
+                    fq = true;
+                }
+                if (key_gt(ps, is, tp, ti) && band_nbr) {
+                    dgv = 1;
+                    src[atomicAdd(&rd->nsrc, 1)] = (int)s;
+                }
+            }
+        }
+        fq_flag[s] = fq ? 1 : 0;
+        dg_flag[s] = dgv;
+    }
+    unsigned c = __popc(__ballot_sync(FULLM, fq));
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->tot_filtered, (unsigned long long)c);
+}
+
+__global__ void kkd_accept_kernel(const uint8_t* __restrict__ fq_flag, const u64* __restrict__ prim,
+                                  const u64* __restrict__ fprim, int64_t n, RoundDev* rd,
+                                  uint8_t* inP, int* cand) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n || !fq_flag[s]) return;
+    if (fprim[s] == prim[s]) {
+        inP[s] = 1;
+        cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+    }
+}
+
+__global__ void pairs_fix_kernel(const int2* __restrict__ pairs, int pair_cap, const uint8_t* inP,
+                                 uint8_t* rej, int iter, RoundDev* rd) {
+    if (iter > 0 && !rd->changed[iter - 1]) return;
+    int np = min(rd->npairs, pair_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < np; t += gridDim.x * blockDim.x) {
+        int2 pr = pairs[t];
+        if (rej[pr.y]) continue;
+        if (!inP[pr.x] || rej[pr.x]) {
+            rej[pr.y] = 1;
+            rd->changed[iter] = 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ removal
+// Removes the accepted candidates unless the round must be settled on the
+// host (danger overflow, or a fixpoint that did not converge in the fixed
+// number of sweeps); candidate marks are cleared in the normal case.
+__global__ void removed_kernel(const int* __restrict__ cand, uint8_t* inP, uint8_t* rej,
+                               uint8_t* alive, RoundDev* rd) {
+    __shared__ int hold;
+    if (threadIdx.x == 0) {
+        hold = rd->overflow || rd->changed[PD_FIX_ITERS - 1];
+        if (hold && blockIdx.x == 0) rd->fix_unconverged = rd->changed[PD_FIX_ITERS - 1];
+    }
+    __syncthreads();
+    if (hold) return;
+    int nc = rd->ncand;
+    unsigned c = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+        int s = cand[t];
+        if (inP[s] && !rej[s]) {
+            alive[s] = 0;
+            c++;
+        }
+        inP[s] = 0;
+        rej[s] = 0;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULLM, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->removed, (unsigned long long)c);
+}
+
+__global__ void dirtyd_kernel(const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
+                              int64_t n, int S, int kchk, uint8_t* dirty, RoundDev* rd) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool d = false;
+    if (s < n) {
+        if (alive[s]) {
+            for (int i = 0; i < kchk; i++) {
+                int x = nbr[s * S + i];
+                if (x >= 0 && !alive[x]) d = true;
+            }
+        }
+        dirty[s] = d ? 1 : 0;
+    }
+    unsigned c = __popc(__ballot_sync(FULLM, d));
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->tot_requery, (unsigned long long)c);
+}
+
+// ------------------------------------------------------------------ k+b buffer
+// Every point stores its S nearest live points exactly, plus the horizon h =
+// the S-th squared distance when they were searched: any point not stored
+// lies at d^2 >= h.  After removals the live stored entries, in order, are
+// still the nearest live points, so as long as k of them remain the new cost
+// follows without a search (the paper's extended k+b neighbourhood, section
+// "Sub-sampling algorithm").  Fewer than k left: the point is searched again.
+#define UPD_SMAX 8
+
+__global__ void kkd_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
+                                  int k, uint8_t* dirty, RoundDev* rd) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool upd = false, req = false;
+    if (s < n) {
+        uint8_t dv = 0;
+        if (alive[s]) {
+            int ids[UPD_SMAX];
+            int r = 0;
+            bool dead = false;
+#pragma unroll
+            for (int i = 0; i < UPD_SMAX; i++) {
+                ids[i] = -1;
+                if (i < S) {
+                    int x = b.nbr[s * S + i];
+                    if (x >= 0) {
+                        if (alive[x]) ids[r++] = x;
+                        else dead = true;
+                    }
+                }
+            }
+            if (dead) {
+                if (r >= k) {
+                    int4 ps = b.pos[s];
+                    u64 h = b.hz[s];
+                    double c = 0.0;
+                    u64 dk = 0, dk1 = ~0ull;
+#pragma unroll
+                    for (int i = 0; i < UPD_SMAX; i++) {
+                        if (i < r && i <= k) {
+                            u64 d2 = sqd(ps, b.pos[ids[i]]);
+                            if (i < k) {
+                                double w = term_weight(b.term, b.weight, b.rgb, b.nrm, (int)s, ids[i]);
+                                c = __dadd_rn(c, __ddiv_rn(w, (double)d2));
+                                dk = d2;
+                            } else {
+                                dk1 = d2;
+                            }
+                        }
+                    }
+                    bool tie = (r > k && dk1 == dk) || (h != ~0ull && dk == h);
+                    b.prim[s] = key_prim_cost(c);
+                    b.rk2[s] = dk;
+                    b.flg[s] = tie ? 1 : 0;
+#pragma unroll
+                    for (int i = 0; i < UPD_SMAX; i++)
+                        if (i < S) b.nbr[s * S + i] = ids[i];
+                    upd = true;
+                } else {
+                    dv = 1;
+                    req = true;
+                }
+            }
+        }
+        dirty[s] = dv;
+    }
+    unsigned cu = __popc(__ballot_sync(FULLM, upd)), cr = __popc(__ballot_sync(FULLM, req));
+    if ((threadIdx.x & 31) == 0) {
+        if (cu) atomicAdd(&rd->tot_updated, (unsigned long long)cu);
+        if (cr) atomicAdd(&rd->tot_requery, (unsigned long long)cr);
+    }
+}
+
+// Candidate test (k >= 2) using the stored buffer where it suffices:
+//   (A) the cost over smaller keys is the cost over the first k stored entries
+//       of smaller key, when k of them are stored (any unstored point is at
+//       least as far as every stored one); otherwise a filtered search.
+//   lam (danger sources): the k-th stored squared distance of key below tau,
+//       when k such entries are stored; otherwise a search.
+__global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
+                                 int k, RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                 uint8_t* lq_flag, u64* lam, int* src) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool fq = false, lq = false;
+    if (s < n) {
+        if (alive[s]) {
+            u64 tp = rd->tau_prim;
+            int ti = rd->tau_idx;
+            u64 ps = b.prim[s];
+            int4 qs = b.pos[s];
+            int is = qs.w;
+            if (!key_gt(tp, ti, ps, is)) {
+                uint8_t fl = b.flg[s];
+                bool lower = !(fl & 1);
+                bool band_nbr = (fl & 1) != 0;
+                int nfound = 0;
+                for (int i = 0; i < S; i++) {
+                    int x = b.nbr[s * S + i];
+                    if (x < 0) continue;
+                    nfound++;
+                    if (i >= k) continue;
+                    u64 px = b.prim[x];
+                    int ix = b.pos[x].w;
+                    if (key_gt(px, ix, ps, is)) lower = false;
+                    if (!key_gt(tp, ti, px, ix)) band_nbr = true;
+                }
+                if (nfound < k) band_nbr = true;
+                bool acc = lower;
+                if (!acc) {
+                    // cost over the stored entries of smaller key
+                    double c = 0.0;
+                    int cnt = 0;
+                    for (int i = 0; i < S && cnt < k; i++) {
+                        int x = b.nbr[s * S + i];
+                        if (x < 0) continue;
+                        int4 px4 = b.pos[x];
+                        if (!key_gt(ps, is, b.prim[x], px4.w)) continue;
+                        double w = term_weight(b.term, b.weight, b.rgb, b.nrm, (int)s, x);
+                        c = __dadd_rn(c, __ddiv_rn(w, (double)sqd(qs, px4)));
+                        cnt++;
+                    }
+                    if (cnt >= k) acc = key_prim_cost(c) == ps;
+                    else fq = true;
+                }
+                if (acc) {
+                    inP[s] = 1;
+                    cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+                }
+                if (key_gt(ps, is, tp, ti) && band_nbr) {
+                    // danger source: lam from the stored entries of key below tau
+                    int cnt = 0;
+                    u64 l = ~0ull;
+                    for (int i = 0; i < S && cnt < k; i++) {
+                        int x = b.nbr[s * S + i];
+                        if (x < 0) continue;
+                        int4 px4 = b.pos[x];
+                        if (!key_gt(tp, ti, b.prim[x], px4.w)) continue;
+                        l = sqd(qs, px4);
+                        cnt++;
+                    }
+                    if (cnt >= k) lam[s] = l;
+                    else lq = true;
+                    src[atomicAdd(&rd->nsrc, 1)] = (int)s;
+                }
+            }
+        }
+        fq_flag[s] = fq ? 1 : 0;
+        lq_flag[s] = lq ? 1 : 0;
+    }
+    unsigned c1 = __popc(__ballot_sync(FULLM, fq)), c2 = __popc(__ballot_sync(FULLM, lq));
+    if ((threadIdx.x & 31) == 0) {
+        if (c1) atomicAdd(&rd->tot_filtered, (unsigned long long)c1);
+        if (c2) atomicAdd(&rd->tot_lambda, (unsigned long long)c2);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+#define GRID1(n) (unsigned)(((n) + 255) / 256), 256
+
+cudaError_t round_launch_setup(RoundDev* rd, cudaStream_t st) {
+    round_setup_kernel<<<1, 32, 0, st>>>(rd); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t round_launch_finish(RoundDev* rd, cudaStream_t st) {
+    round_finish_kernel<<<1, 32, 0, st>>>(rd); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
+                                SelBuffers& b, RoundDev* rd, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) blocks = 1;
+    for (int pass = 0; pass < 8; pass++) {
+        seld_hist_kernel<<<blocks, 256, 0, st>>>(prim, alive, n, b.p[0], b.i[0], b.p[1], b.i[1],
+                                                 pass, rd, b.hist); note_launch();
+        seld_find_kernel<<<1, 256, 0, st>>>(b.hist, pass, rd); note_launch();
+        if (pass < 7) {
+            seld_compact_kernel<<<blocks, 256, 0, st>>>(prim, pos, alive, n, b.p[0], b.i[0],
+                                                        b.p[1], b.i[1], pass, rd); note_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
+                            const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
+                            RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
+                            cudaStream_t st) {
+    k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, flg, n, S, rd, inP, cand, slow); note_launch();
+    k1d_slow_kernel<<<PERSIST_BLOCKS, 128, 0, st>>>(g, prim, alive, rk2, slow, rd, inP, cand); note_launch();
+    for (int it = 0; it < PD_FIX_ITERS; it++) {
+        k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, g.pos, nbr, S, inP, rej, it, rd); note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_kk_cand(const u64* prim, const int4* pos, const uint8_t* alive,
+                                 const int* nbr, const uint8_t* flg, int64_t n, int S, int k,
+                                 RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                 uint8_t* dg_flag, int* src, cudaStream_t st) {
+    kkd_cand_kernel<<<GRID1(n), 0, st>>>(prim, pos, alive, nbr, flg, n, S, k, rd, inP, cand,
+                                         fq_flag, dg_flag, src); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
+                                   int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
+                                   cudaStream_t st) {
+    kkd_accept_kernel<<<GRID1(n), 0, st>>>(fq_flag, prim, fprim, n, rd, inP, cand); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_pairs_fix(const int2* pairs, int pair_cap, const uint8_t* inP,
+                                   uint8_t* rej, RoundDev* rd, cudaStream_t st) {
+    for (int it = 0; it < PD_FIX_ITERS; it++) {
+        pairs_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(pairs, pair_cap, inP, rej, it, rd); note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_remove(const int* cand, uint8_t* inP, uint8_t* rej, uint8_t* alive,
+                                RoundDev* rd, cudaStream_t st) {
+    removed_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, inP, rej, alive, rd); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t round_launch_dirty(const uint8_t* alive, const int* nbr, int64_t n, int S, int kchk,
+                               uint8_t* dirty, RoundDev* rd, cudaStream_t st) {
+    dirtyd_kernel<<<GRID1(n), 0, st>>>(alive, nbr, n, S, kchk, dirty, rd); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pd
+
+namespace pd {
+cudaError_t round_launch_kk_update(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
+                                   uint8_t* dirty, RoundDev* rd, cudaStream_t st) {
+    kkd_update_kernel<<<GRID1(n), 0, st>>>(b, alive, n, S, k, dirty, rd); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t round_launch_kk_cand2(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
+                                  RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
+                                  uint8_t* lq_flag, u64* lam, int* src, cudaStream_t st) {
+    kkd_cand2_kernel<<<GRID1(n), 0, st>>>(b, alive, n, S, k, rd, inP, cand, fq_flag, lq_flag, lam,
+                                          src); note_launch();
+    return cudaGetLastError();
+}
+}  // namespace pd
