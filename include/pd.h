@@ -160,6 +160,37 @@ int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_ho
                      const float* normals_host, int64_t n, const pd_cost_params* cp, int64_t m,
                      uint8_t* keep_host, void* stream, pd_stats* stats /* may be NULL */);
 
+/*
+ * Allocation-free variant of the neighbour/cost pass (no counterpart in the
+ * paper: it exists for callers that cannot allocate device memory when they
+ * call us, e.g. a real-time ingest loop whose memory budget is fixed at
+ * start-up, or a plug-in that must not touch its host's allocator).
+ *
+ * Computes exactly what pd_build_grid (default parameters) followed by
+ * pd_knn_cost with the density cost (term PD_TERM_NONE) computes, for clouds
+ * of at most PD_STATIC_MAX_POINTS points:
+ *   xyz_dev   n x 3 int32, device, caller-owned (read only).
+ *   cost_dev  n doubles, device (may be NULL);  knn_dev n x k int32, device
+ *             (may be NULL) -- the same layout as pd_knn_cost.
+ * All temporaries live in one file-scope device array of
+ * PD_STATIC_SCRATCH_BYTES bytes that every GPU loading the library holds until
+ * the process exits.  The call makes no cudaMalloc / cudaFree / cudaMallocAsync
+ * and uses no allocating library routine.  The first call on a device looks
+ * up the array's device address on that device (cudaGetSymbolAddress) and
+ * caches it: make that first call before any stream capture.  Every call
+ * reuses the same array and overwrites it; it clears what must start at
+ * zero.  Two calls that overlap on the GPU (different streams, devices sharing
+ * nothing else) race on the array: serialise them.  The call synchronises the
+ * stream (it reads the cloud's extent and cell count, like pd_build_grid).
+ * Returns PD_EINVAL (NULL xyz, n < 1, k outside [1, 16]), PD_ERANGE (n above
+ * PD_STATIC_MAX_POINTS, or a coordinate spread >= 2^25 mm), PD_ENOMEM (the
+ * cloud needs more octree cells than the fixed table holds), PD_ECUDA.
+ */
+#define PD_STATIC_MAX_POINTS 65536
+#define PD_STATIC_SCRATCH_BYTES (16u << 20)
+int pd_knn_cost_static(const int32_t* xyz_dev, int64_t n, int k, double* cost_dev,
+                       int32_t* knn_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

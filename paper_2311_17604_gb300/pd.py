@@ -19,10 +19,11 @@ LIB_PATH = os.path.join(_HERE, "libpd.so")
 PD_OK, PD_EINVAL, PD_ERANGE, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EINTERNAL = range(7)
 PD_TERM_NONE, PD_TERM_COLOR, PD_TERM_ORIENT = 0, 1, 2
 PD_KMAX = 16
+PD_STATIC_MAX_POINTS = 65536
 
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
-            "pd_grid_stats", "pd_decimate_host"]
+            "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static"]
 
 
 class PdError(RuntimeError):
@@ -90,6 +91,7 @@ def lib():
         L.pd_grid_stats.argtypes = [P, ctypes.POINTER(pd_stats)]
         L.pd_decimate_host.argtypes = [P, P, P, P, I64, ctypes.POINTER(pd_cost_params), I64, P,
                                        P, ctypes.POINTER(pd_stats)]
+        L.pd_knn_cost_static.argtypes = [P, I64, ctypes.c_int, P, P, P]
         for f in EXPORTED:
             if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -273,3 +275,22 @@ def pd_decimate_host(ctx: Context, xyz: np.ndarray, m, k=1, term=PD_TERM_NONE, w
                                 int(m), _ptr(keep), _stream_ptr(stream), ctypes.byref(st))
     ctx.check(rc, "pd_decimate_host")
     return keep, st.as_dict()
+
+
+def pd_knn_cost_static(xyz, k=1, cost=None, knn=None, stream=None):
+    """Allocation-free neighbour/cost pass for clouds of at most
+    PD_STATIC_MAX_POINTS points (device int32 [n,3]); same outputs as
+    pd_knn_cost with the density cost.  Raises PdError on failure."""
+    torch = _torch()
+    assert xyz.is_cuda and xyz.dtype == torch.int32 and xyz.dim() == 2 and xyz.shape[1] == 3
+    xyz = xyz.contiguous()
+    n = int(xyz.shape[0])
+    if cost is None:
+        cost = torch.empty(n, dtype=torch.float64, device=xyz.device)
+    if knn is None:
+        knn = torch.empty((n, k), dtype=torch.int32, device=xyz.device)
+    rc = lib().pd_knn_cost_static(_ptr(xyz), n, int(k), _ptr(cost), _ptr(knn),
+                                  _stream_ptr(stream))
+    if rc:
+        raise PdError(rc, "pd_knn_cost_static")
+    return cost, knn
