@@ -102,6 +102,8 @@ typedef struct {
     double ms_knn_requery;    /* re-searches of points that lost a neighbour */
     double ms_rules;          /* removal-rule kernels and key selection */
     int64_t launches;         /* kernels launched by the call */
+    double ms_select;         /* of rules: on-device selection of the key threshold */
+    double ms_danger;         /* of rules: k >= 2 danger-pair analysis */
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */

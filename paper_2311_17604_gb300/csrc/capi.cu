@@ -756,6 +756,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     // lower keys inside), grown again while yields stay high.  Any band gives
     // the same result; only the number of rounds changes.
     double band_max = cp->band > 0 ? cp->band : 0.02;
+    // small clouds: examine at least ~4096 keys per round
+    if (cp->band <= 0 && g->n > 0) band_max = std::max(band_max, std::min(0.5, 4096.0 / g->n));
     int64_t live = g->n;
     // ---- duplicate phase
     int64_t nd = 0;
@@ -779,7 +781,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     int kchk = g->density_k1 ? S : k;
     bool use_buf = !g->density_k1 && S <= 8;
     uint8_t *inP, *rej, *dirty, *fqf = nullptr, *dgf = nullptr;  // dgf: lambda search flags
-    int *cand, *slow, *src = nullptr;
+    int *cand, *slow, *src = nullptr, *csort = nullptr;
     u64 *fprim = nullptr, *lam = nullptr;
     int2* pairs = nullptr;
     int64_t cap = g->n;
@@ -795,6 +797,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         ALLOC(fqf, uint8_t, cap);
         ALLOC(dgf, uint8_t, cap);
         ALLOC(src, int, cap);
+        ALLOC(csort, int, cap);
         ALLOC(fprim, u64, cap);
         ALLOC(lam, u64, cap);
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
@@ -832,7 +835,10 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         }
         GridView v = view_of(g);
         CK(round_launch_setup(rd, g->st));
-        CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+        {
+            Span t(T, &g->stats.ms_select);
+            CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+        }
         if (g->density_k1) {
             CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
                                rej, cand, slow, g->st));
@@ -851,8 +857,13 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
                 rc = knn_flag(g, cp, FILT_BELOW_TAU, Sf, dgf, lam, rd);
                 if (rc) return rc;
             }
-            CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k, pairs,
-                                   pair_cap, rd, g->st));
+            {
+                Span t(T, &g->stats.ms_danger);
+                // candidates in Morton order, so each source finds its own by search
+                CK(stable_compact(inP, g->ng, csort, &rd->ncs, scratch_of(g), g->st));
+                CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k,
+                                       pairs, pair_cap, csort, rd, g->st));
+            }
             CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
         }
         CK(round_launch_remove(cand, inP, rej, g->alive, rd, g->st));
@@ -916,7 +927,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.danger_queries = (int64_t)h.tot_lambda;
     CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
     CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
-    void* fr[] = {inP, rej, dirty, cand, slow, src, fqf, dgf, fprim, lam, pairs,
+    void* fr[] = {inP, rej, dirty, cand, slow, src, csort, fqf, dgf, fprim, lam, pairs,
                   sb.p[0], sb.p[1], sb.i[0], sb.i[1], sb.hist, rd};
     for (void* p : fr) gfree(g, p);
     cudaEventRecord(e1, g->st);

@@ -137,7 +137,7 @@ template <int S, int FILT, typename D>
 __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, uint32_t b,
                                            uint32_t e, int q, int4 qp, bool todo, u64 tp, int ti,
                                            TopList<S>& top, int4* sp, u64* sk, int* so,
-                                           int lane) {
+                                           int lane, int sub, int lpq) {
     for (uint32_t c = b; c < e; c += 32) {
         uint32_t j = c + lane;
         int4 v = make_int4(0, 0, 0, -1);
@@ -155,7 +155,7 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
         int m = (int)min(32u, e - c);
         if (todo) {
             D worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
-            for (int t = 0; t < m; t++) {
+            for (int t = sub; t < m; t += lpq) {
                 int4 cv = sp[t];
                 if (cv.w < 0 || cv.w == q) continue;
                 if (FILT != FILT_NONE) {
@@ -194,7 +194,20 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
         q = a.list ? a.list[G.x + lane] : G.x + lane;
         if (a.qflag && !a.qflag[q]) q = -1;
     }
-    if (!__any_sync(FULLM, q >= 0)) return;
+    // pack the active queries onto the 32 lanes: with nq queries each gets
+    // lpq = 32 / nq (power of two) lanes that split every staged chunk; their
+    // partial lists are merged before the exactness test
+    unsigned act = __ballot_sync(FULLM, q >= 0);
+    if (!act) return;
+    int nq = __popc(act);
+    int lpq = 32;
+    while (lpq > 1 && nq * lpq > 32) lpq >>= 1;
+    int qi = lane / lpq, sub = lane - qi * lpq;
+    {
+        int srcl = qi < nq ? (int)__fns(act, 0, qi + 1) : 0;
+        int qq = __shfl_sync(FULLM, q, srcl);
+        q = qi < nq ? qq : -1;
+    }
     int q0 = a.list ? a.list[G.x] : G.x;
     u64 c0 = g.code[q0];
     int4 qp = q >= 0 ? g.pos[q] : make_int4(0, 0, 0, 0);
@@ -252,16 +265,35 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
             if (__all_sync(FULLM, skip)) continue;
             if (lv + g.shift <= 13)
                 scan_range<S, FILT, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
-                                              s_o[w], lane);
+                                              s_o[w], lane, sub, lpq);
             else
                 scan_range<S, FILT, u64>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
-                                         s_o[w], lane);
+                                         s_o[w], lane, sub, lpq);
+        }
+        // merge the partial lists of each query's lanes (butterfly)
+        for (int off = lpq >> 1; off >= 1; off >>= 1) {
+            u64 od[S];
+            int oi[S];
+#pragma unroll
+            for (int i = 0; i < S; i++) {
+                od[i] = __shfl_xor_sync(FULLM, top.d[i], off);
+                oi[i] = __shfl_xor_sync(FULLM, top.id[i], off);
+            }
+            if (todo) {
+#pragma unroll
+                for (int i = 0; i < S; i++) {
+                    if (od[i] != ~0ull && (od[i] < top.d[S - 1] ||
+                                           (od[i] == top.d[S - 1] && oi[i] < top.id[S - 1])))
+                        top.insert(od[i], oi[i]);
+                }
+            }
         }
         if (todo) {
             u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
             u64 bound = top.at(R - 1);
             if (gg == ~0ull || bound < gg) {
                 todo = false;
+                if (sub == 0) {  // one lane per query writes the result
                 int found = 0;
 #pragma unroll
                 for (int i = 0; i < S; i++) found += top.d[i] != ~0ull;
@@ -302,6 +334,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
                     }
                 } else {
                     a.lam_out[q] = top.at(a.k - 1);
+                }
                 }
             } else {
                 top.init();

@@ -64,7 +64,7 @@ struct RoundDev {
     int done;
     unsigned pre[8];
     int len[2];
-    int ncand, nslow, nsrc, npairs, overflow;
+    int ncand, nslow, nsrc, npairs, overflow, ncs;
     int changed[PD_FIX_ITERS];
     int fix_unconverged;
     int density_k1;
@@ -139,7 +139,7 @@ cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, cons
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
-                                int pair_cap, RoundDev* rd, cudaStream_t st);
+                                int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_pairs_fix(const int2* pairs, int pair_cap, const uint8_t* inP,
                                    uint8_t* rej, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_remove(const int* cand, uint8_t* inP, uint8_t* rej, uint8_t* alive,

@@ -360,7 +360,8 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
                            const uint8_t* __restrict__ alive, const uint8_t* __restrict__ inP,
                            uint8_t* rej, const u64* __restrict__ lam, const int* __restrict__ nbr,
                            int S, int k, int2* pairs, int* npairs, int pair_cap, int* overflow,
-                           unsigned long long* diag, DangerSmem& sm, int w, int lane) {
+                           unsigned long long* diag, const int* __restrict__ csorted,
+                           const int* __restrict__ ncs, DangerSmem& sm, int w, int lane) {
     int(&c_j)[DG_WARPS][DG_CAP] = sm.c_j;
     u64(&c_d)[DG_WARPS][DG_CAP] = sm.c_d;
     int4(&st_p)[DG_WARPS][32] = sm.st_p;
@@ -396,17 +397,42 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
                        rl + g.shift);
         if (rbox >= lx) rt = 0;
     }
-    // 1. candidates
+    // 1. candidates: when a Morton-sorted list of them is given, each range
+    // [b, e) maps to a slice of that list by binary search; otherwise the
+    // range's points are streamed and filtered
     int nc = 0;
+    uint32_t cs_lo = 0, cs_hi = 0;
+    if (csorted && rt) {
+        int nlist = *ncs;
+        int lo = 0, hi = nlist;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if ((uint32_t)csorted[mid] < rb) lo = mid + 1;
+            else hi = mid;
+        }
+        cs_lo = (uint32_t)lo;
+        hi = nlist;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if ((uint32_t)csorted[mid] < re) lo = mid + 1;
+            else hi = mid;
+        }
+        cs_hi = (uint32_t)lo;
+    }
     for (int r = 0; r < 27; r++) {
         int tr = __shfl_sync(FULLM, rt, r);
         if (!tr) continue;
         uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
+        if (csorted) {
+            b = __shfl_sync(FULLM, cs_lo, r);
+            e = __shfl_sync(FULLM, cs_hi, r);
+        }
         for (uint32_t c = b; c < e; c += 32) {
-            uint32_t j = c + lane;
+            uint32_t jj = c + lane;
+            uint32_t j = (csorted && jj < e) ? (uint32_t)csorted[jj] : jj;
             bool take = false;
             u64 d2 = 0;
-            if (j < e && (int)j != x && alive[j] && inP[j]) {
+            if (jj < e && (int)j != x && alive[j] && inP[j]) {
                 int4 v = g.pos[j];
                 long long ddx = v.x - xp.x, ddy = v.y - xp.y, ddz = v.z - xp.z;
                 d2 = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
@@ -524,13 +550,14 @@ __global__ void __launch_bounds__(DG_WARPS * 32)
                   const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
                   const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
                   const int* __restrict__ nbr, int S, int k, int2* pairs, int* npairs,
-                  int pair_cap, int* overflow, unsigned long long* diag) {
+                  int pair_cap, int* overflow, unsigned long long* diag,
+                  const int* __restrict__ csorted, const int* __restrict__ ncs) {
     __shared__ DangerSmem sm;
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int ns = *nsrc;
     for (int t = blockIdx.x * DG_WARPS + w; t < ns; t += gridDim.x * DG_WARPS)
         danger_one(g, src[t], prim, alive, inP, rej, lam, nbr, S, k, pairs, npairs, pair_cap,
-                   overflow, diag, sm, w, lane);
+                   overflow, diag, csorted, ncs, sm, w, lane);
 }
 
 // Fallback: accept every live point with key >= tau (tau = the top key).
@@ -730,17 +757,17 @@ cudaError_t launch_danger(const GridView& g, const int* src, const int* nsrc, in
     unsigned blocks = (unsigned)((max_src + DG_WARPS - 1) / DG_WARPS);
     danger_kernel<<<blocks, DG_WARPS * 32, 0, st>>>(g, src, nsrc, prim, alive, inP, rej, lam,
                                                     nullptr, 0, k, pairs, npairs, pair_cap,
-                                                    overflow, diag); note_launch();
+                                                    overflow, diag, nullptr, nullptr); note_launch();
     return cudaGetLastError();
 }
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
-                                int pair_cap, RoundDev* rd, cudaStream_t st) {
+                                int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
     danger_kernel<<<152 * 4, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
-                                                     &rd->cap_over); note_launch();
+                                                     &rd->cap_over, csorted, &rd->ncs); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_accept_above(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
