@@ -80,9 +80,11 @@ typedef struct {
     int32_t term;             /* PD_TERM_* */
     double weight;            /* weight of the colour / orientation term */
     const float* normals_dev; /* n x 3 float32, input order (PD_TERM_ORIENT) */
-    double band;              /* k >= 2: fraction of live points examined per
-                                 removal round (0 = default 0.02); never
-                                 changes the result */
+    double band;              /* fraction of live points examined per removal
+                                 round (k >= 2 or weighted costs); 0 = default
+                                 (0.02, at least 4096 points; 0.01 with a
+                                 colour/orientation term).  Never changes a
+                                 density-cost result. */
     int32_t reserved[6];
 } pd_cost_params;
 
@@ -161,6 +163,30 @@ int pd_grid_stats(const pd_grid* grid, pd_stats* out);
 int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_host,
                      const float* normals_host, int64_t n, const pd_cost_params* cp, int64_t m,
                      uint8_t* keep_host, void* stream, pd_stats* stats /* may be NULL */);
+
+/*
+ * Batch of independent scans (many clouds of uneven size).  Scans run through
+ * `concurrency` slots (0 = 8); each slot has its own stream and host thread
+ * and runs pd_build_grid + pd_decimate_count on its scans, so the slots'
+ * kernels overlap on the device.  Every scan gets the same result it gets
+ * alone.  The work is ordered after what is queued on `stream`, and `stream`
+ * waits for all of it; the call returns when every scan is done.
+ * Returns PD_OK, or the first error of any scan (each scan's own status is in
+ * its descriptor).
+ */
+typedef struct {
+    const int32_t* xyz_dev;    /* n x 3 int32, device */
+    const uint8_t* rgb_dev;    /* n x 3 uint8, device, or NULL */
+    const float* normals_dev;  /* n x 3 float32, device, or NULL */
+    int64_t n;
+    int64_t m;                 /* points to keep; < 0: floor(ratio * n) */
+    double ratio;
+    uint8_t* keep_dev;         /* n bytes, device (output) */
+    int32_t status;            /* output: PD_OK or an error code */
+    pd_stats stats;            /* output */
+} pd_scan_desc;
+int pd_decimate_batch(pd_ctx* ctx, pd_scan_desc* scans, int nscans, const pd_cost_params* cp,
+                      int concurrency, void* stream);
 
 /*
  * Allocation-free variant of the neighbour/cost pass (no counterpart in the

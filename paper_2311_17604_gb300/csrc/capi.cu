@@ -6,6 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/pd.h"
@@ -67,10 +70,13 @@ struct pd_ctx {
     pd_allocator alloc;
     int has_alloc;
     char err[512];
+    std::mutex mu;  // guards err (batch slots report errors concurrently)
 };
 
 static void set_err(pd_ctx* c, const char* fmt, const char* a = "", long long b = 0) {
-    if (c) snprintf(c->err, sizeof(c->err), fmt, a, b);
+    if (!c) return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    snprintf(c->err, sizeof(c->err), fmt, a, b);
 }
 
 static void* ctx_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) {
@@ -225,8 +231,10 @@ int build_cells(pd_grid* g) {
 // ============================================================ API: context
 extern "C" int pd_ctx_create(const pd_allocator* alloc, pd_ctx** out) {
     if (!out) return PD_EINVAL;
-    pd_ctx* c = (pd_ctx*)calloc(1, sizeof(pd_ctx));
+    pd_ctx* c = new (std::nothrow) pd_ctx();
     if (!c) return PD_ENOMEM;
+    c->has_alloc = 0;
+    c->err[0] = 0;
     if (alloc && alloc->alloc && alloc->free) {
         c->alloc = *alloc;
         c->has_alloc = 1;
@@ -235,7 +243,7 @@ extern "C" int pd_ctx_create(const pd_allocator* alloc, pd_ctx** out) {
     return PD_OK;
 }
 
-extern "C" void pd_ctx_destroy(pd_ctx* ctx) { free(ctx); }
+extern "C" void pd_ctx_destroy(pd_ctx* ctx) { delete ctx; }
 
 extern "C" const char* pd_strerror(int code) {
     switch (code) {
@@ -758,6 +766,10 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     double band_max = cp->band > 0 ? cp->band : 0.02;
     // small clouds: examine at least ~4096 keys per round
     if (cp->band <= 0 && g->n > 0) band_max = std::max(band_max, std::min(0.5, 4096.0 / g->n));
+    // colour / orientation weights make costs non-monotone (a removal can
+    // raise a neighbour's cost), so the rounds are no longer provably the
+    // sequential order: a narrow band keeps them close to it
+    if (cp->band <= 0 && cp->term != PD_TERM_NONE) band_max = 0.01;
     int64_t live = g->n;
     // ---- duplicate phase
     int64_t nd = 0;
@@ -1087,3 +1099,74 @@ extern "C" int pd__debug_first_pass(pd_grid* g, const pd_cost_params* cp, int64_
 
 // Internal: kernels launched by this library so far in the process.
 extern "C" long long pd__launch_count(void) { return g_launch_count; }
+
+// ============================================================ API: batch
+// Many independent scans through a fixed number of concurrent slots: every
+// slot owns a CUDA stream and a host thread that builds the scan's grid and
+// runs its removal rounds; the slots' kernels overlap on the device.  The
+// call orders all work after what is already queued on `stream` and makes
+// `stream` wait for all of it before returning.
+extern "C" int pd_decimate_batch(pd_ctx* ctx, pd_scan_desc* scans, int nscans,
+                                 const pd_cost_params* cp, int concurrency, void* stream) {
+    if (!ctx || !scans || nscans < 0 || !cp) return PD_EINVAL;
+    if (nscans == 0) return PD_OK;
+    for (int i = 0; i < nscans; i++) {
+        const pd_scan_desc& d = scans[i];
+        if (!d.xyz_dev || !d.keep_dev || d.n < 1 ||
+            (d.m < 0 && !(d.ratio >= 0.0 && d.ratio <= 1.0)) || d.m > d.n) {
+            set_err(ctx, "pd_decimate_batch: invalid scan descriptor %s%lld", "", i);
+            return PD_EINVAL;
+        }
+    }
+    int slots = concurrency > 0 ? concurrency : 8;
+    if (slots > nscans) slots = nscans;
+    int dev = 0;
+    if (cudaGetDevice(&dev)) return PD_ECUDA;
+    cudaStream_t caller = (cudaStream_t)stream;
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) return PD_ECUDA;
+    cudaEventRecord(start, caller);
+    std::vector<cudaStream_t> st(slots);
+    std::vector<cudaEvent_t> fin(slots);
+    for (int s = 0; s < slots; s++) {
+        cudaStreamCreateWithFlags(&st[s], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&fin[s], cudaEventDisableTiming);
+        cudaStreamWaitEvent(st[s], start, 0);
+    }
+    std::atomic<int> next(0);
+    std::atomic<int> first_err(PD_OK);
+    auto worker = [&](int slot) {
+        cudaSetDevice(dev);
+        for (;;) {
+            int i = next.fetch_add(1);
+            if (i >= nscans) break;
+            pd_scan_desc& d = scans[i];
+            pd_grid* g = nullptr;
+            int rc = pd_build_grid(ctx, d.xyz_dev, d.rgb_dev, d.n, nullptr, st[slot], &g);
+            if (!rc) {
+                pd_cost_params c2 = *cp;
+                if (d.normals_dev) c2.normals_dev = d.normals_dev;
+                int64_t m = d.m >= 0 ? d.m : (int64_t)(d.ratio * (double)d.n);
+                rc = pd_decimate_count(g, &c2, m, d.keep_dev, st[slot]);
+                if (!rc) pd_grid_stats(g, &d.stats);
+            }
+            if (g) pd_grid_free(g);
+            d.status = rc;
+            if (rc) {
+                int expect = PD_OK;
+                first_err.compare_exchange_strong(expect, rc);
+            }
+        }
+        cudaEventRecord(fin[slot], st[slot]);
+    };
+    std::vector<std::thread> th;
+    for (int s = 0; s < slots; s++) th.emplace_back(worker, s);
+    for (auto& t : th) t.join();
+    for (int s = 0; s < slots; s++) {
+        cudaStreamWaitEvent(caller, fin[s], 0);
+        cudaEventDestroy(fin[s]);
+        cudaStreamDestroy(st[s]);
+    }
+    cudaEventDestroy(start);
+    return first_err.load();
+}

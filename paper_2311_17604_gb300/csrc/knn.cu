@@ -23,8 +23,16 @@ namespace pd {
 
 #define FULLM 0xffffffffu
 
+// The S smallest (d^2, input index) pairs; id holds the Morton position.
+// Equal distances are ordered by input index, as in the definition's reading
+// (it matters only when neighbour weights differ, i.e. colour/orientation).
+template <int S, bool W>
+struct TopList;
+
+// Density costs: any order among equal distances gives the same cost, so the
+// Morton position serves as the tie order (no extra registers).
 template <int S>
-struct TopList {
+struct TopList<S, false> {
     u64 d[S];
     int id[S];
     __device__ __forceinline__ void init() {
@@ -34,7 +42,11 @@ struct TopList {
             id[i] = 0x7fffffff;
         }
     }
-    __device__ __forceinline__ void insert(u64 dd, int j) {
+    __device__ __forceinline__ int tie(int i) const { return id[i]; }
+    __device__ __forceinline__ bool beats_last(u64 dd, int j, int) const {
+        return dd < d[S - 1] || (dd == d[S - 1] && j < id[S - 1]);
+    }
+    __device__ __forceinline__ void insert(u64 dd, int j, int) {
         d[S - 1] = dd;
         id[S - 1] = j;
 #pragma unroll
@@ -46,6 +58,50 @@ struct TopList {
             d[i] = sw ? b : a;
             id[i - 1] = sw ? x : y;
             id[i] = sw ? y : x;
+        }
+    }
+    __device__ __forceinline__ u64 at(int r) const {
+        u64 v = d[0];
+#pragma unroll
+        for (int i = 1; i < S; i++)
+            if (i == r) v = d[i];
+        return v;
+    }
+};
+
+template <int S>
+struct TopList<S, true> {
+    u64 d[S];
+    int id[S];
+    int oi[S];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            d[i] = ~0ull;
+            id[i] = 0x7fffffff;
+            oi[i] = 0x7fffffff;
+        }
+    }
+    __device__ __forceinline__ int tie(int i) const { return oi[i]; }
+    __device__ __forceinline__ bool beats_last(u64 dd, int, int o) const {
+        return dd < d[S - 1] || (dd == d[S - 1] && o < oi[S - 1]);
+    }
+    __device__ __forceinline__ void insert(u64 dd, int j, int o) {
+        d[S - 1] = dd;
+        id[S - 1] = j;
+        oi[S - 1] = o;
+#pragma unroll
+        for (int i = S - 1; i > 0; i--) {
+            bool sw = d[i] < d[i - 1] || (d[i] == d[i - 1] && oi[i] < oi[i - 1]);
+            u64 a = d[i], b = d[i - 1];
+            int x = id[i], y = id[i - 1];
+            int u = oi[i], v = oi[i - 1];
+            d[i - 1] = sw ? a : b;
+            d[i] = sw ? b : a;
+            id[i - 1] = sw ? x : y;
+            id[i] = sw ? y : x;
+            oi[i - 1] = sw ? u : v;
+            oi[i] = sw ? v : u;
         }
     }
     __device__ __forceinline__ u64 at(int r) const {
@@ -119,8 +175,8 @@ __device__ inline double nbr_weight(const KnnArgs& a, int q, int j) {
     return 1.0;
 }
 
-template <int S>
-__device__ inline double cost_sum(const KnnArgs& a, int q, const TopList<S>& top, int k) {
+template <int S, bool W>
+__device__ inline double cost_sum(const KnnArgs& a, int q, const TopList<S, W>& top, int k) {
     double c = 0.0;
 #pragma unroll
     for (int i = 0; i < S; i++) {
@@ -133,10 +189,10 @@ __device__ inline double cost_sum(const KnnArgs& a, int q, const TopList<S>& top
 }
 
 // Stream one range [b, e) of Morton positions against every lane's query.
-template <int S, int FILT, typename D>
+template <int S, int FILT, bool W, typename D>
 __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, uint32_t b,
                                            uint32_t e, int q, int4 qp, bool todo, u64 tp, int ti,
-                                           TopList<S>& top, int4* sp, u64* sk, int* so,
+                                           TopList<S, W>& top, int4* sp, u64* sk, int* so,
                                            int lane, int sub, int lpq) {
     for (uint32_t c = b; c < e; c += 32) {
         uint32_t j = c + lane;
@@ -144,10 +200,8 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
         if (j < e) {
             v = g.pos[j];
             bool ok = !a.alive || a.alive[j];
-            if (FILT != FILT_NONE) {
-                sk[lane] = a.prim[j];
-                so[lane] = v.w;
-            }
+            if (FILT != FILT_NONE) sk[lane] = a.prim[j];
+            if (FILT != FILT_NONE || W) so[lane] = v.w;
             v.w = ok ? (int)j : -1;
         }
         sp[lane] = v;
@@ -168,8 +222,9 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
                 } else {
                     dd = (D)((long long)dx * dx) + (D)((long long)dy * dy) + (D)((long long)dz * dz);
                 }
-                if (dd < worst || (dd == worst && cv.w < top.id[S - 1])) {
-                    top.insert((u64)dd, cv.w);
+                int co = W ? so[t] : cv.w;
+                if (dd < worst || (dd == worst && co < top.tie(S - 1))) {
+                    top.insert((u64)dd, cv.w, co);
                     worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
                 }
             }
@@ -178,7 +233,7 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
     }
 }
 
-template <int S, int FILT>
+template <int S, int FILT, bool W>
 __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs a) {
     __shared__ int4 s_p[PD_WARPS][32];
     __shared__ u64 s_k[PD_WARPS][32];
@@ -226,7 +281,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
     // searches: all S stored neighbours exact (the k+b neighbour buffer, so a
     // removal can be absorbed without a new search); filtered searches: k.
     const int R = FILT == FILT_NONE ? (a.density_k1 ? 1 : S) : a.k;
-    TopList<S> top;
+    TopList<S, W> top;
     top.init();
     bool todo = q >= 0;
     while (__any_sync(FULLM, todo)) {
@@ -264,28 +319,27 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
             }
             if (__all_sync(FULLM, skip)) continue;
             if (lv + g.shift <= 13)
-                scan_range<S, FILT, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
-                                              s_o[w], lane, sub, lpq);
+                scan_range<S, FILT, W, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w],
+                                                 s_k[w], s_o[w], lane, sub, lpq);
             else
-                scan_range<S, FILT, u64>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
-                                         s_o[w], lane, sub, lpq);
+                scan_range<S, FILT, W, u64>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
+                                            s_o[w], lane, sub, lpq);
         }
         // merge the partial lists of each query's lanes (butterfly)
         for (int off = lpq >> 1; off >= 1; off >>= 1) {
             u64 od[S];
-            int oi[S];
+            int oj[S], oo[S];
 #pragma unroll
             for (int i = 0; i < S; i++) {
                 od[i] = __shfl_xor_sync(FULLM, top.d[i], off);
-                oi[i] = __shfl_xor_sync(FULLM, top.id[i], off);
+                oj[i] = __shfl_xor_sync(FULLM, top.id[i], off);
+                oo[i] = W ? __shfl_xor_sync(FULLM, top.tie(i), off) : oj[i];
             }
             if (todo) {
 #pragma unroll
-                for (int i = 0; i < S; i++) {
-                    if (od[i] != ~0ull && (od[i] < top.d[S - 1] ||
-                                           (od[i] == top.d[S - 1] && oi[i] < top.id[S - 1])))
-                        top.insert(od[i], oi[i]);
-                }
+                for (int i = 0; i < S; i++)
+                    if (od[i] != ~0ull && top.beats_last(od[i], oj[i], oo[i]))
+                        top.insert(od[i], oj[i], oo[i]);
             }
         }
         if (todo) {
@@ -317,7 +371,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
 #pragma unroll
                         for (int i = 0; i < S; i++)
                             a.nbr[(int64_t)q * S + i] = top.d[i] != ~0ull ? top.id[i] : -1;
-                        double c = cost_sum<S>(a, q, top, k);
+                        double c = cost_sum<S, W>(a, q, top, k);
                         a.prim_out[q] = key_prim_cost(c);
                         u64 dk = top.at(k - 1);
                         a.rk2_out[q] = dk;
@@ -330,7 +384,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
                     if (a.density_k1) {
                         a.fprim_out[q] = key_prim_d2(top.d[0]);
                     } else {
-                        a.fprim_out[q] = key_prim_cost(cost_sum<S>(a, q, top, a.k));
+                        a.fprim_out[q] = key_prim_cost(cost_sum<S, W>(a, q, top, a.k));
                     }
                 } else {
                     a.lam_out[q] = top.at(a.k - 1);
@@ -348,7 +402,11 @@ template <int S, int FILT>
 static cudaError_t launch_knn_t(const GridView& g, const KnnArgs& a, cudaStream_t st) {
     if (a.ngroups <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((a.ngroups + PD_WARPS - 1) / PD_WARPS);
-    knn_kernel<S, FILT><<<blocks, PD_WARPS * 32, 0, st>>>(g, a); note_launch();
+    if (a.term != 0)
+        knn_kernel<S, FILT, true><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+    else
+        knn_kernel<S, FILT, false><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ PD_STATIC_MAX_POINTS = 65536
 
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
-            "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static"]
+            "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch"]
 
 
 class PdError(RuntimeError):
@@ -65,6 +65,13 @@ class pd_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class pd_scan_desc(ctypes.Structure):
+    _fields_ = [("xyz_dev", ctypes.c_void_p), ("rgb_dev", ctypes.c_void_p),
+                ("normals_dev", ctypes.c_void_p), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("ratio", ctypes.c_double), ("keep_dev", ctypes.c_void_p),
+                ("status", ctypes.c_int32), ("stats", pd_stats)]
+
+
 _lib = None
 
 
@@ -93,6 +100,8 @@ def lib():
         L.pd_decimate_host.argtypes = [P, P, P, P, I64, ctypes.POINTER(pd_cost_params), I64, P,
                                        P, ctypes.POINTER(pd_stats)]
         L.pd_knn_cost_static.argtypes = [P, I64, ctypes.c_int, P, P, P]
+        L.pd_decimate_batch.argtypes = [P, ctypes.POINTER(pd_scan_desc), ctypes.c_int,
+                                        ctypes.POINTER(pd_cost_params), ctypes.c_int, P]
         for f in EXPORTED:
             if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -295,3 +304,32 @@ def pd_knn_cost_static(xyz, k=1, cost=None, knn=None, stream=None):
     if rc:
         raise PdError(rc, "pd_knn_cost_static")
     return cost, knn
+
+
+def pd_decimate_batch(ctx: Context, clouds, k=1, term=PD_TERM_NONE, weight=0.0, concurrency=0,
+                      band=0.0, stream=None):
+    """Decimate many independent scans; ``clouds`` is a list of dicts with
+    ``xyz`` (device int32 [n,3]), ``m`` or ``ratio``, optional ``rgb`` (device
+    uint8 [n,3]) and ``normals`` (device float32 [n,3]).  Returns the keep
+    masks (device uint8) and per-scan stats."""
+    torch = _torch()
+    descs = (pd_scan_desc * len(clouds))()
+    keeps = []
+    for i, c in enumerate(clouds):
+        x = c["xyz"].contiguous()
+        c["xyz"] = x
+        n = int(x.shape[0])
+        keep = torch.empty(n, dtype=torch.uint8, device=x.device)
+        keeps.append(keep)
+        descs[i].xyz_dev = x.data_ptr()
+        descs[i].rgb_dev = c["rgb"].data_ptr() if c.get("rgb") is not None else None
+        descs[i].normals_dev = c["normals"].data_ptr() if c.get("normals") is not None else None
+        descs[i].n = n
+        descs[i].m = int(c["m"]) if c.get("m") is not None else -1
+        descs[i].ratio = float(c.get("ratio", 0.0))
+        descs[i].keep_dev = keep.data_ptr()
+    cp = cost_params(k, term, weight, None, band)
+    rc = lib().pd_decimate_batch(ctx.h, descs, len(clouds), ctypes.byref(cp), int(concurrency),
+                                 _stream_ptr(stream))
+    ctx.check(rc, "pd_decimate_batch")
+    return keeps, [descs[i].stats.as_dict() for i in range(len(clouds))]
