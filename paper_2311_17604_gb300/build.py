@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpd.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["grid.cu", "knn.cu", "rounds.cu", "rounds_dev.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["grid.cu", "knn.cu", "rounds.cu", "rounds_dev.cu", "capi.cu", "noalloc.cu", "normals.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     """Build libpd.so if any source changed; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "pd.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     extra = list(extra or [])
     objs, jobs = [], []
     for src in SOURCES:

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/pd.h"
+#include "../../include/pd_normals.h"
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
 
@@ -1099,6 +1100,37 @@ extern "C" int pd__debug_first_pass(pd_grid* g, const pd_cost_params* cp, int64_
 
 // Internal: kernels launched by this library so far in the process.
 extern "C" long long pd__launch_count(void) { return g_launch_count; }
+
+// ============================================================ hooks for normals.cu
+namespace pd {
+void* api_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) { return ctx_alloc(c, bytes, st); }
+void api_free(pd_ctx* c, void* p, cudaStream_t st) { ctx_free(c, p, st); }
+void api_error(pd_ctx* c, const char* what, long long v) { set_err(c, "%s (%lld)", what, v); }
+
+// The 16 nearest neighbours of every grid point, ascending (d^2, input index),
+// stored as Morton positions in the grid's neighbour array (width S = 17).
+int grid_knn16(pd_grid* g, cudaStream_t st, GridNbrs* out) {
+    g->st = st;
+    if (g->ng != g->n) {
+        set_err(g->ctx, "pd_normals_pca: grid already decimated%s", "", 0);
+        return PD_EINVAL;
+    }
+    pd_cost_params cp;
+    memset(&cp, 0, sizeof(cp));
+    cp.k = PD_NORMAL_K;
+    int rc = prepare_state(g, &cp);
+    if (rc) return rc;
+    KnnArgs a = base_args(g, &cp);
+    a.term = PD_TERM_INDEX_TIE;
+    CK(launch_knn(view_of(g), a, g->st));
+    out->pos = g->pos;
+    out->nbr = g->nbr;
+    out->S = g->S;
+    out->n = g->ng;
+    out->ctx = g->ctx;
+    return PD_OK;
+}
+}  // namespace pd
 
 // ============================================================ API: batch
 // Many independent scans through a fixed number of concurrent slots: every

@@ -110,6 +110,9 @@ struct KnnArgs {
     u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
 };
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
+// Internal neighbour-weight term: unit weights with equal distances ordered by
+// input index (the normals' 16-NN order).
+#define PD_TERM_INDEX_TIE 3
 
 // ---------------------------------------------------------------- rounds.cu
 struct SelectResult {
@@ -163,4 +166,38 @@ cudaError_t round_launch_kk_update(const BufView& b, const uint8_t* alive, int64
 cudaError_t round_launch_kk_cand2(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
                                   RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
                                   uint8_t* lq_flag, u64* lam, int* src, cudaStream_t st);
+}  // namespace pd
+
+// ---------------------------------------------------------------- normals.cu
+struct pd_ctx;
+struct pd_grid;
+namespace pd {
+struct GridNbrs {
+    const int4* pos;
+    const int* nbr;  // n x S Morton positions, nearest first, -1 past the found ones
+    int S;
+    int64_t n;
+    pd_ctx* ctx;
+};
+// capi.cu: context allocator, error text, and the 16-NN pass over a grid
+void* api_alloc(pd_ctx* c, size_t bytes, cudaStream_t st);
+void api_free(pd_ctx* c, void* p, cudaStream_t st);
+void api_error(pd_ctx* c, const char* what, long long v);
+int grid_knn16(pd_grid* g, cudaStream_t st, GridNbrs* out);
+cudaError_t launch_features(const int4* pos, const int* nbr, int S, int64_t n, uint16_t* feat,
+                            float* pca, uint8_t* valid, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* prm, const uint16_t* feat, const int* rows, int64_t n,
+                               float* outn, float* onorm, float* h1s, float* h2s, float* raw,
+                               cudaStream_t st);
+cudaError_t launch_mlp_backward(const float* prm, const uint16_t* feat, const int* rows,
+                                const float* labels, int64_t n, const float* h1s,
+                                const float* h2s, const float* raw, float* grad, float* loss,
+                                cudaStream_t st);
+cudaError_t launch_adam(float* prm, float* m, float* v, const float* grad, int t, float lr,
+                        cudaStream_t st);
+cudaError_t launch_mlp_init(float* prm, u64 seed, cudaStream_t st);
+cudaError_t launch_sample_rows(const int* pool, int64_t npool, u64 seed, long long t, int b,
+                               int* rows, cudaStream_t st);
+cudaError_t launch_normal_fallback(const float* mlp, const float* onorm, const float* pca,
+                                   int64_t n, float min_norm, float* out, cudaStream_t st);
 }  // namespace pd

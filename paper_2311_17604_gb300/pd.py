@@ -23,7 +23,13 @@ PD_STATIC_MAX_POINTS = 65536
 
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
-            "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch"]
+            "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch",
+            # pd_normals.h
+            "pd_normals_pca", "pd_mlp_init", "pd_mlp_forward", "pd_mlp_grad", "pd_mlp_train",
+            "pd_normals_mlp"]
+PD_NORMAL_K, PD_MLP_IN, PD_MLP_HIDDEN = 16, 48, 64
+PD_NORMAL_DEFINED, PD_NORMAL_PLANAR = 1, 2
+PD_MLP_PARAMS = 64 * 48 + 64 + 64 * 64 + 64 + 3 * 64 + 3
 
 
 class PdError(RuntimeError):
@@ -75,6 +81,11 @@ class pd_scan_desc(ctypes.Structure):
 _lib = None
 
 
+class pd_train_params(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
 def lib():
     """The loaded libpd.so (raises if it has not been built)."""
     global _lib
@@ -102,6 +113,13 @@ def lib():
         L.pd_knn_cost_static.argtypes = [P, I64, ctypes.c_int, P, P, P]
         L.pd_decimate_batch.argtypes = [P, ctypes.POINTER(pd_scan_desc), ctypes.c_int,
                                         ctypes.POINTER(pd_cost_params), ctypes.c_int, P]
+        L.pd_normals_pca.argtypes = [P, P, P, P, P]
+        L.pd_mlp_init.argtypes = [P, ctypes.c_uint64, P]
+        L.pd_mlp_forward.argtypes = [P, P, I64, P, P, P]
+        L.pd_mlp_grad.argtypes = [P, P, P, P, I64, P, P, P]
+        L.pd_mlp_train.argtypes = [P, P, P, ctypes.c_int, P, P, P, I64,
+                                   ctypes.POINTER(pd_train_params), P, P]
+        L.pd_normals_mlp.argtypes = [P, P, P, P, I64, ctypes.c_float, P, P]
         for f in EXPORTED:
             if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -333,3 +351,86 @@ def pd_decimate_batch(ctx: Context, clouds, k=1, term=PD_TERM_NONE, weight=0.0, 
                                  _stream_ptr(stream))
     ctx.check(rc, "pd_decimate_batch")
     return keeps, [descs[i].stats.as_dict() for i in range(len(clouds))]
+
+
+# ---------------------------------------------------------------- normals (pd_normals.h)
+def pd_normals_pca(grid: Grid, stream=None):
+    """16-NN feature rows (bfloat16 bit patterns, int16 tensor [n, 48]), PCA
+    normals (float32 [n, 3]) and validity (uint8 [n]) of every grid point."""
+    torch = _torch()
+    feat = torch.empty((grid.n, PD_MLP_IN), dtype=torch.int16, device="cuda")
+    pca = torch.empty((grid.n, 3), dtype=torch.float32, device="cuda")
+    valid = torch.empty(grid.n, dtype=torch.uint8, device="cuda")
+    rc = lib().pd_normals_pca(grid.h, _ptr(feat), _ptr(pca), _ptr(valid), _stream_ptr(stream))
+    grid.ctx.check(rc, "pd_normals_pca")
+    return feat, pca, valid
+
+
+def pd_mlp_init(seed=0, params=None, stream=None):
+    torch = _torch()
+    if params is None:
+        params = torch.empty(PD_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    rc = lib().pd_mlp_init(_ptr(params), int(seed), _stream_ptr(stream))
+    if rc:
+        raise PdError(rc, "pd_mlp_init")
+    return params
+
+
+def pd_mlp_forward(params, feat, stream=None):
+    """Network normals (float32 [n, 3]) and raw output norms (float32 [n])."""
+    torch = _torch()
+    n = int(feat.shape[0])
+    normals = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    norm = torch.empty(n, dtype=torch.float32, device="cuda")
+    rc = lib().pd_mlp_forward(_ptr(params), _ptr(feat), n, _ptr(normals), _ptr(norm),
+                              _stream_ptr(stream))
+    if rc:
+        raise PdError(rc, "pd_mlp_forward")
+    return normals, norm
+
+
+def pd_mlp_grad(ctx: Context, params, feat, labels, stream=None):
+    """(mean loss, gradient float32 [PD_MLP_PARAMS]) over all rows."""
+    torch = _torch()
+    grad = torch.empty(PD_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    rc = lib().pd_mlp_grad(ctx.h, _ptr(params), _ptr(feat), _ptr(labels.contiguous()),
+                           int(feat.shape[0]), _ptr(grad), _ptr(loss), _stream_ptr(stream))
+    ctx.check(rc, "pd_mlp_grad")
+    return float(loss.item()), grad
+
+
+class MlpTrainer:
+    """Parameters plus Adam state, trained in place by pd_mlp_train."""
+
+    def __init__(self, seed=0, params=None):
+        torch = _torch()
+        self.params = pd_mlp_init(seed) if params is None else params
+        self.adam = torch.zeros(2 * PD_MLP_PARAMS, dtype=torch.float32, device="cuda")
+        self.step = 0
+
+    def train(self, ctx: Context, feat, labels, valid=None, steps=100, batch=4096, lr=1e-3,
+              seed=0, stream=None):
+        """Runs `steps` Adam steps; returns the per-step batch losses (float32)."""
+        torch = _torch()
+        loss = torch.empty(max(steps, 1), dtype=torch.float32, device="cuda")
+        tp = pd_train_params(int(steps), int(batch), float(lr), int(seed))
+        rc = lib().pd_mlp_train(ctx.h, _ptr(self.params), _ptr(self.adam), self.step, _ptr(feat),
+                                _ptr(labels.contiguous()), _ptr(valid), int(feat.shape[0]),
+                                ctypes.byref(tp), _ptr(loss), _stream_ptr(stream))
+        ctx.check(rc, "pd_mlp_train")
+        self.step += steps
+        return loss[:steps]
+
+
+def pd_normals_mlp(ctx: Context, params, feat, pca, min_norm=0.0, stream=None):
+    """Normals for the orientation term: network where its output norm is at
+    least min_norm (default 1e-3), PCA elsewhere; params=None gives PCA."""
+    torch = _torch()
+    n = int(pca.shape[0])
+    out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    rc = lib().pd_normals_mlp(ctx.h, _ptr(params), _ptr(feat), _ptr(pca), n, float(min_norm),
+                              _ptr(out), _stream_ptr(stream))
+    ctx.check(rc, "pd_normals_mlp")
+    return out
+
