@@ -26,9 +26,13 @@ EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "
             "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch",
             # pd_normals.h
             "pd_normals_pca", "pd_mlp_init", "pd_mlp_forward", "pd_mlp_grad", "pd_mlp_train",
-            "pd_normals_mlp"]
+            "pd_normals_mlp",
+            # pd_serve.h
+            "pd_serve_open", "pd_serve_submit", "pd_serve_poll", "pd_serve_counts",
+            "pd_serve_close"]
 PD_NORMAL_K, PD_MLP_IN, PD_MLP_HIDDEN = 16, 48, 64
 PD_NORMAL_DEFINED, PD_NORMAL_PLANAR = 1, 2
+PD_SERVE_BYTES_PER_POINT, PD_SERVE_BYTES_PER_POINT_NORMALS = 240, 400
 PD_MLP_PARAMS = 64 * 48 + 64 + 64 * 64 + 64 + 3 * 64 + 3
 
 
@@ -81,6 +85,19 @@ class pd_scan_desc(ctypes.Structure):
 _lib = None
 
 
+class pd_serve_params(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("mem_budget", ctypes.c_int64),
+                ("cost", pd_cost_params), ("mlp_params_dev", ctypes.c_void_p),
+                ("normals", ctypes.c_int)]
+
+
+class pd_serve_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("stats", pd_stats)]
+
+
 class pd_train_params(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("seed", ctypes.c_uint64)]
@@ -120,9 +137,16 @@ def lib():
         L.pd_mlp_train.argtypes = [P, P, P, ctypes.c_int, P, P, P, I64,
                                    ctypes.POINTER(pd_train_params), P, P]
         L.pd_normals_mlp.argtypes = [P, P, P, P, I64, ctypes.c_float, P, P]
+        L.pd_serve_open.argtypes = [P, ctypes.POINTER(pd_serve_params), ctypes.POINTER(P)]
+        L.pd_serve_submit.argtypes = [P, P, P, I64, I64, ctypes.c_double, P]
+        L.pd_serve_poll.argtypes = [P, I64, ctypes.c_int, ctypes.POINTER(pd_serve_result)]
+        L.pd_serve_counts.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                      ctypes.POINTER(I64)]
+        L.pd_serve_close.argtypes = [P]
         for f in EXPORTED:
             if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
                 getattr(L, f).restype = ctypes.c_int
+        L.pd_serve_submit.restype = I64
         _lib = L
     return _lib
 
@@ -433,4 +457,77 @@ def pd_normals_mlp(ctx: Context, params, feat, pca, min_norm=0.0, stream=None):
                               _ptr(out), _stream_ptr(stream))
     ctx.check(rc, "pd_normals_mlp")
     return out
+
+
+# ---------------------------------------------------------------- serving (pd_serve.h)
+class Server:
+    """pd_serve_* request loop.  ``submit`` takes host numpy arrays (kept
+    alive here until the scan is polled done); page-locked arrays from
+    ``pinned_like`` let the copies run asynchronously."""
+
+    def __init__(self, ctx: Context, slots=4, mem_budget=0, k=1, term=PD_TERM_NONE, weight=0.0,
+                 mlp_params=None, normals=False, band=0.0):
+        self.ctx = ctx
+        p = pd_serve_params()
+        p.slots = int(slots)
+        p.mem_budget = int(mem_budget)
+        p.cost = cost_params(k, term, weight, None, band)
+        p.mlp_params_dev = None if mlp_params is None else mlp_params.data_ptr()
+        p.normals = 1 if normals else 0
+        self._mlp = mlp_params
+        h = ctypes.c_void_p()
+        rc = lib().pd_serve_open(ctx.h, ctypes.byref(p), ctypes.byref(h))
+        ctx.check(rc, "pd_serve_open")
+        self.h = h
+        self._live = {}
+
+    def submit(self, xyz, m=-1, ratio=0.0, rgb=None, keep=None):
+        """Queue one scan (host int32 [n,3]); returns its ticket."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32) if isinstance(xyz, np.ndarray) else xyz
+        n = int(xyz.shape[0])
+        if keep is None:
+            keep = np.empty(n, dtype=np.uint8)
+        t = lib().pd_serve_submit(self.h, _ptr(xyz), _ptr(rgb), n, int(m), float(ratio),
+                                  _ptr(keep))
+        if t < 0:
+            raise PdError(int(-t), "pd_serve_submit")
+        self._live[int(t)] = (xyz, rgb, keep)
+        return int(t)
+
+    def poll(self, ticket, wait_ms=-1):
+        """(keep mask, result dict) when done, else None."""
+        r = pd_serve_result()
+        rc = lib().pd_serve_poll(self.h, int(ticket), int(wait_ms), ctypes.byref(r))
+        if rc == PD_ETIMEOUT:
+            return None
+        if rc:
+            raise PdError(rc, "pd_serve_poll")
+        keep = self._live[int(ticket)][2]
+        res = {f: getattr(r, f) for f, _ in pd_serve_result._fields_ if f != "stats"}
+        res["stats"] = r.stats.as_dict()
+        return keep, res
+
+    def counts(self):
+        q, r, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib().pd_serve_counts(self.h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(d))
+        return q.value, r.value, d.value
+
+    def close(self):
+        if self.h:
+            lib().pd_serve_close(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pinned_like(a):
+    """A page-locked copy of a numpy array (a numpy view of a pinned torch tensor)."""
+    torch = _torch()
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t.numpy()
 
