@@ -12,6 +12,12 @@ keeping 10 % of the points.
   e2e     the same through pd_decimate_host (host buffers, copies timed)
   roofline  the first full kNN/cost pass: algorithmic bytes / launch time
   cpu_baseline  the CPU oracle on a bounded sector of the same scan
+  batched   many room scans of uneven size (sizes log-uniform 50k-5M, RGB,
+            colour term 0.3, keep 5-50 %) through pd_decimate_batch, against
+            the same scans one at a time; per-scan p50/p99 ms
+  serving   Poisson arrivals (50 scans/s) of room scans of 100k-10M points
+            through the pd_serve_* loop with the orientation term and network
+            normals; p50/p99 latency, throughput, normal angular error
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
        python bench.py --impl reference ...   (the CPU oracle as the reference arm)
@@ -169,6 +175,140 @@ def run_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+
+# ------------------------------------------------------------------ batched and served legs
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def run_batched(args, pd, torch, dev, stream):
+    """A batch of room scans shaped like the 512-scan workload (sizes
+    log-uniform in 50k-5M, room size and scanner from the seed, RGB, colour
+    term 0.3, k = 1, keep 5-50 %), bounded to --batch-count scans."""
+    import oracle
+    specs = synth.batch_specs(seed=0, count=args.batch_count, n_lo=5e4, n_hi=5e6)
+    clouds, total = [], 0
+    for sp in specs:
+        s = synth.room_scan(seed=sp["seed"], n_az=sp["n_az"], n_el=sp["n_el"], dims=sp["dims"],
+                            scanner=sp["scanner"], rgb=True)
+        clouds.append({"xyz": torch.from_numpy(s.xyz).to(dev), "rgb": torch.from_numpy(s.rgb).to(dev),
+                       "ratio": sp["ratio"]})
+        total += s.n
+    ctx = pd.Context()
+    kw = dict(k=1, term=pd.PD_TERM_COLOR, weight=0.3)
+    pd.pd_decimate_batch(ctx, clouds[:4], concurrency=4, stream=stream, **kw)   # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    keeps, stats = pd.pd_decimate_batch(ctx, clouds, concurrency=args.batch_slots,
+                                        stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    for c, kp in zip(clouds, keeps):
+        assert int(kp.sum().item()) == oracle.target_count(int(c["xyz"].shape[0]), c["ratio"])
+    # the same scans one at a time through the single-scan path
+    e0.record(stream)
+    for c in clouds:
+        g = pd.Grid(ctx, c["xyz"], rgb=c["rgb"], stream=stream)
+        pd.pd_decimate_ratio(g, c["ratio"], stream=stream, **kw)
+        g.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    per_scan = [st["ms_total"] for st in stats]
+    ctx.close()
+    return {"workload": "%d room scans, sizes log-uniform 50k-5M (%d points), RGB, k=1 + 0.3 x "
+                        "colour term, keep U[5%%, 50%%]" % (len(clouds), total),
+            "scans": len(clouds), "points": total, "slots": args.batch_slots,
+            "value": total / (batch_ms / 1e3), "unit": UNIT, "ms": batch_ms,
+            "single_scan_loop": {"value": total / (single_ms / 1e3), "ms": single_ms},
+            "speedup_vs_single": single_ms / batch_ms,
+            "per_scan_ms": {"p50": _pct(per_scan, 50), "p99": _pct(per_scan, 99),
+                            "what": "each scan's decimation time on its slot's stream"}}
+
+
+def run_serving(args, pd, torch, dev):
+    """Poisson arrivals of room scans (n log-uniform in 100k-10M) at --serve-rate
+    scans/s through pd_serve_*, orientation term 0.5 with network normals."""
+    from oracle import normals as onorm  # angle helper only (reporting)
+    rng = np.random.default_rng(0)
+    # a pool of distinct scans, reused round-robin by the requests
+    sizes = np.exp(rng.uniform(np.log(1e5), np.log(1e7), args.serve_pool))
+    pool = []
+    for i, sz in enumerate(sizes):
+        n_el = max(10, int(round(np.sqrt(sz / 5.0))))
+        s = synth.room_scan(seed=100 + i, n_az=5 * n_el, n_el=n_el)
+        pool.append((pd.pinned_like(s.xyz), s.n))
+    ctx = pd.Context(use_torch_allocator=False)
+    # the network: trained on the PCA normals of the planar rows of one scan
+    tr_scan = synth.room_scan(seed=99, n_az=1000, n_el=200)
+    g = pd.Grid(ctx, torch.from_numpy(tr_scan.xyz).to(dev))
+    feat, pca, valid = pd.pd_normals_pca(g)
+    g.free()
+    trainer = pd.MlpTrainer(seed=0)
+    t0 = time.perf_counter()
+    losses = trainer.train(ctx, feat, pca, ((valid & pd.PD_NORMAL_PLANAR) != 0).to(torch.uint8),
+                           steps=args.train_steps, batch=4096, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # angular error of the network against PCA on an unseen pool scan
+    x0 = torch.from_numpy(np.asarray(pool[0][0])).to(dev)
+    g = pd.Grid(ctx, x0)
+    feat, pca, valid = pd.pd_normals_pca(g)
+    g.free()
+    u, _ = pd.pd_mlp_forward(trainer.params, feat)
+    planar = ((valid & pd.PD_NORMAL_PLANAR) != 0).cpu().numpy()
+    ang = onorm.angle(u.cpu().numpy()[planar], pca.cpu().numpy()[planar])
+    ratio, k, w = 0.25, 4, 0.5
+    srv = pd.Server(ctx, slots=args.serve_slots, k=k, term=pd.PD_TERM_ORIENT, weight=w,
+                    mlp_params=trainer.params, normals=True)
+    # warm: one small request
+    srv.poll(srv.submit(pool[int(np.argmin(sizes))][0], ratio=ratio))
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, args.serve_requests))
+    tickets, t_start = [], time.perf_counter()
+    for i, at in enumerate(arrivals):
+        d = at - (time.perf_counter() - t_start)
+        if d > 0:
+            time.sleep(d)
+        x, n = pool[i % len(pool)]
+        tickets.append((srv.submit(x, ratio=ratio), n))
+    res = [(srv.poll(t)[1], n) for t, n in tickets]
+    srv.close()
+    lat = [r["t_done_ms"] - r["t_submit_ms"] for r, _ in res]
+    qwait = [r["t_admit_ms"] - r["t_submit_ms"] for r, _ in res]
+    span_ms = max(r["t_done_ms"] for r, _ in res) - min(r["t_submit_ms"] for r, _ in res)
+    pts = sum(n for _, n in res)
+    assert all(r["status"] == 0 for r, _ in res)
+    # the plain single-scan path on the same pool, one scan at a time
+    t0 = time.perf_counter()
+    for x, n in pool:
+        xd = torch.from_numpy(np.asarray(x)).to(dev)
+        g = pd.Grid(ctx, xd)
+        feat, pca, _ = pd.pd_normals_pca(g)
+        nrm = pd.pd_normals_mlp(ctx, trainer.params, feat, pca)
+        pd.pd_decimate_ratio(g, ratio, k=k, term=pd.PD_TERM_ORIENT, weight=w, normals=nrm)
+        g.free()
+    torch.cuda.synchronize()
+    single_s = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "%d requests, Poisson %.0f scans/s, room scans n log-uniform 100k-10M "
+                        "(pool of %d, mean %.2fM), k=%d + %.1f x orientation term, network "
+                        "normals, keep %g%%" % (args.serve_requests, args.serve_rate,
+                                                 len(pool), np.mean([n for _, n in pool]) / 1e6,
+                                                 k, w, 100 * ratio),
+            "slots": args.serve_slots,
+            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat)},
+            "queue_wait_ms": {"p50": _pct(qwait, 50), "p99": _pct(qwait, 99)},
+            "throughput": pts / (span_ms / 1e3), "unit": UNIT,
+            "offered": float(np.mean([n for _, n in pool]) * args.serve_rate),
+            "single_scan_path": {"value": sum(n for _, n in pool) / single_s,
+                                 "what": "pool scans one at a time, host-timed, inputs on device"},
+            "normals": {"train_steps": args.train_steps, "train_s": train_s,
+                        "final_loss": float(losses[-20:].mean().item()),
+                        "angle_vs_pca_deg": {"median": float(np.degrees(np.median(ang))),
+                                             "p90": float(np.degrees(np.percentile(ang, 90)))}}}
+
 def run_gpu(args, wl, rank, world, local_rank, dist):
     import torch
 
@@ -275,6 +415,11 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
                "sample": "first %d points (azimuth sector) of the scan, k=%d, keep %g; kNN "
                          "on %d threads, greedy single-threaded; %.1f s"
                          % (nsmp, k, wl["ratio"], threads, dt)}
+    batched = serving = None
+    if world == 1 and not args.no_batch:
+        batched = run_batched(args, pd, torch, dev, stream)
+    if world == 1 and not args.no_serve:
+        serving = run_serving(args, pd, torch, dev)
     mean = {key: statistics.mean(s[key] for s in stats) for key in stats[0]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
@@ -285,6 +430,7 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
                        "l2": "256 MiB buffer written between timed steps; working set > L2"},
             "e2e": e2e,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "batched": batched, "serving": serving,
             "gpu_launches": int(launches),
             "detail": {"rounds": mean["rounds"], "ms_knn": mean["ms_knn"],
                        "ms_build": mean["ms_build"], "ms_rules": mean["ms_rules"],
@@ -304,6 +450,15 @@ def main(argv=None):
     ap.add_argument("--workload", default="outdoor", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--batch-count", type=int, default=48)
+    ap.add_argument("--batch-slots", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-pool", type=int, default=12)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--knn-only", action="store_true",
                     help="profiling aid: build the grid and run one full kNN/cost pass")
     args = ap.parse_args(argv)
