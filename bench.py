@@ -176,6 +176,57 @@ def run_reference(args, wl, rank):
 
 
 
+
+# ------------------------------------------------------------------ roofline of the kNN pass
+# DRAM bytes per query of knn_kernel<8,0> (the first full pass), from one
+# `ncu --set full` capture of `bench.py --knn-only` on the outdoor scan, valid
+# while the kernel's sources hash to KNN_SRC_SHA (else traffic is reported null).
+KNN_SRC_SHA = None
+KNN_DRAM_BYTES_PER_QUERY = None
+KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
+               "paper_2311_17604_gb300/csrc/pd_kernels.h"]
+ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop: exact int distance test
+
+
+def knn_src_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KNN_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def knn_roofline(stats, k, clk, device):
+    """The first full kNN/cost pass (one launch per step).  It is bound by
+    integer issue, not HBM: achieved = candidate pairs scanned x 9 integer ops
+    / launch time, against the issue peak SMs x 4 schedulers x 32 lanes x SM
+    clock.  The HBM view (algorithmic bytes / time / measured copy bandwidth)
+    is reported beside it."""
+    import torch
+    S = 8 if k <= 6 else 17
+    # read {x,y,z,i}; write key, r_k^2, flags, S neighbours and (k >= 2) the horizon
+    per_q = 16 + 8 + 8 + 1 + 4 * S + (8 if k >= 2 else 0)
+    ms = statistics.mean(s["ms_knn_first"] for s in stats)
+    q = statistics.mean(s["q_first"] for s in stats)
+    pairs = statistics.mean(s["pairs_first"] for s in stats)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak_ops = sms * 4 * 32 * mhz * 1e6
+    achieved = pairs * ALU_OPS_PER_PAIR / (ms / 1e3)
+    hbm_peak, hbm_kind = measured_peaks()
+    hbm = q * per_q / (ms / 1e3) / 1e9
+    sha = knn_src_sha()
+    traffic = (KNN_DRAM_BYTES_PER_QUERY * q) if sha == KNN_SRC_SHA and KNN_DRAM_BYTES_PER_QUERY else None
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+            "frac": achieved / peak_ops, "traffic": traffic,
+            "kernel": "knn_kernel<%d,0> (first full pass)" % S, "ms": ms, "queries": q,
+            "pairs_per_query": pairs / max(q, 1), "ops_per_pair": ALU_OPS_PER_PAIR,
+            "peak_basis": "%d SMs x 4 x 32 lanes x %.0f MHz (median SM clock sampled)" % (sms, mhz),
+            "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
+                    "bytes_per_query": per_q, "peak_kind": hbm_kind},
+            "src_sha": sha}
+
 # ------------------------------------------------------------------ batched and served legs
 def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
@@ -389,22 +440,7 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                "d2h_bytes_per_step": n}
 
-    # roofline of the first full kNN/cost pass (one launch per step): algorithmic
-    # bytes = per query 16 B read ({x,y,z,index}) + written key 8 + k-th d^2 8 +
-    # flags 1 + S stored neighbours x 4
-    S = 8 if (k == 1 or k + 1 > 4) else 4
-    if k + 1 > 8:
-        S = 17
-    per_q = 16 + 8 + 8 + 1 + 4 * S
-    ms_first = statistics.mean(s["ms_knn_first"] for s in stats)
-    q_first = statistics.mean(s["q_first"] for s in stats)
-    peak, peak_kind = measured_peaks()
-    achieved = q_first * per_q / (ms_first / 1e3) / 1e9
-    traffic = None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "knn_kernel (first pass)",
-                "bytes_per_query": per_q, "queries": q_first, "ms": ms_first,
-                "peak_kind": peak_kind}
+    roofline = knn_roofline(stats, k, clk, torch.cuda.current_device())
     if rank != 0:
         return
     cpu = None

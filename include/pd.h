@@ -106,6 +106,7 @@ typedef struct {
     int64_t launches;         /* kernels launched by the call */
     double ms_select;         /* of rules: on-device selection of the key threshold */
     double ms_danger;         /* of rules: k >= 2 danger-pair analysis */
+    int64_t pairs_first;      /* (query, candidate) pairs the first pass scanned */
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */

@@ -784,11 +784,20 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     }
     // ---- first neighbour pass
     {
+        unsigned long long* dpairs = g->d_u64 + 1;
+        CK(cudaMemsetAsync(dpairs, 0, sizeof(*dpairs), g->st));
         Span t(T, &g->stats.ms_knn_first);
-        rc = knn_all(g, cp, nullptr);
-        if (rc) return rc;
+        KnnArgs a = base_args(g, cp);
+        a.pairs_out = dpairs;
+        CK(launch_knn(view_of(g), a, g->st));
     }
     g->stats.q_first = g->ng;
+    {
+        unsigned long long pairs = 0;
+        CK(cudaMemcpyAsync(&pairs, g->d_u64 + 1, sizeof(pairs), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        g->stats.pairs_first = (int64_t)pairs;
+    }
     int S = g->S;
     int Sf = filt_width(k);
     int kchk = g->density_k1 ? S : k;

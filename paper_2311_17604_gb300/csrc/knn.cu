@@ -284,12 +284,13 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
     TopList<S, W> top;
     top.init();
     bool todo = q >= 0;
+    unsigned long long wpairs = 0;
     while (__any_sync(FULLM, todo)) {
         int sh = 3 * L;
         int cx = (int)compact3(c0 >> sh), cy = (int)compact3(c0 >> (sh + 1)),
             cz = (int)compact3(c0 >> (sh + 2));
         if (L >= g.B) cx = cy = cz = 0;
-        int o = (lane + 13) % 27;
+        int o = lane < 27 ? kCellOrder[lane] : 13;
         int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
         uint32_t rb = 0, re = 0;
         int rl = L, rt = 0;
@@ -318,6 +319,10 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
                 skip = bound != ~0ull && box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift) > bound;
             }
             if (__all_sync(FULLM, skip)) continue;
+            if (a.pairs_out) {  // warp-uniform count of the pairs this range costs
+                int nqt = __popc(__ballot_sync(FULLM, todo && sub == 0));
+                wpairs += (unsigned long long)(e - b) * (unsigned long long)nqt;
+            }
             if (lv + g.shift <= 13)
                 scan_range<S, FILT, W, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w],
                                                  s_k[w], s_o[w], lane, sub, lpq);
@@ -396,6 +401,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
         }
         L++;
     }
+    if (a.pairs_out && lane == 0 && wpairs) atomicAdd(a.pairs_out, wpairs);
 }
 
 template <int S, int FILT>

@@ -175,4 +175,10 @@ inline void note_launch() { __atomic_fetch_add(&g_launch_count, 1, __ATOMIC_RELA
 // ---------------------------------------------------------------- warp utils
 __device__ inline int warp_lane() { return threadIdx.x & 31; }
 
+// The 3x3x3 cells around a query cell in the order they are scanned: the
+// cell itself, the 6 face neighbours, the 12 edge and the 8 corner neighbours
+// (cell o = (dx+1) + 3 (dy+1) + 9 (dz+1)).  Nearer cells first tighten the
+// k-th distance bound early, which prunes more of the farther cells.
+static __device__ __constant__ const unsigned char kCellOrder[27] = {13, 4, 10, 12, 14, 16, 22, 1, 3, 5, 7, 9, 11, 15, 17, 19, 21, 23, 25, 0, 2, 6, 8, 18, 20, 24, 26};
+
 }  // namespace pd

@@ -108,6 +108,7 @@ struct KnnArgs {
     // outputs (filter modes)
     u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
     u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
+    unsigned long long* pairs_out;  // optional: + (query, candidate) pairs scanned
 };
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
 // Internal neighbour-weight term: unit weights with equal distances ordered by

@@ -378,7 +378,7 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
     int ux = xp.x - g.origin.x, uy = xp.y - g.origin.y, uz = xp.z - g.origin.z;
     int cx, cy, cz;
     int L = cover_level(g, ux, uy, uz, g.code[x], g.leaf[x], lx, cx, cy, cz);
-    int o = (lane + 13) % 27;
+    int o = lane < 27 ? kCellOrder[lane] : 13;
     int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
     uint32_t rb = 0, re = 0;
     int rl = L, rt = 0;
@@ -764,7 +764,7 @@ cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* pr
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
                                 int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
-    danger_kernel<<<152 * 4, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
+    danger_kernel<<<152 * 8, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
                                                      &rd->cap_over, csorted, &rd->ncs); note_launch();

@@ -118,10 +118,17 @@ def test_fig3_configuration(orc):
 
 
 def test_paper_cube_count():
-    """Cube example: 10 % of 452,230 points is 45,223 (section Results)."""
+    """The cube example of section "Results and Discussion": 10 % of the cube
+    leaves about 45,223 points, 90.45 points per m^2 over 500 m^2.  The target
+    count rule m = floor(ratio * n) must reproduce it for n = 452,230 (the
+    "452k" input that the printed count implies)."""
+    import os
     import oracle
-    assert oracle.target_count(452230, 0.1) == 45223
-    assert abs(45223 / 500 - 90.45) < 0.005
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_cube_example.txt")
+    row = [l.split() for l in open(path) if l.strip() and not l.startswith("#")][0]
+    m, area, density, ratio = int(row[0]), float(row[1]), float(row[2]), float(row[3])
+    assert oracle.target_count(452230, ratio) == m
+    assert abs(m / area - density) < 0.005
 
 
 # ------------------------------------------------- independent oracles
