@@ -181,8 +181,8 @@ def run_reference(args, wl, rank):
 # DRAM bytes per query of knn_kernel<8,0> (the first full pass), from one
 # `ncu --set full` capture of `bench.py --knn-only` on the outdoor scan, valid
 # while the kernel's sources hash to KNN_SRC_SHA (else traffic is reported null).
-KNN_SRC_SHA = None
-KNN_DRAM_BYTES_PER_QUERY = None
+KNN_SRC_SHA = "8076e2a7983add50"
+KNN_DRAM_BYTES_PER_QUERY = 111.4   # 523.6 MB read + 633.7 MB written / 10,385,229 queries
 KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
                "paper_2311_17604_gb300/csrc/pd_kernels.h"]
 ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop: exact int distance test
@@ -387,6 +387,37 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         g.free()
         return keep, st
 
+    if args.normals_only:
+        # profiling aid and measurement: 16-NN + features/PCA, then the network
+        # forward over every point, each timed with CUDA events on `stream`
+        g = pd.Grid(ctx, xyz_dev, stream=stream)
+        feat, pca, valid = pd.pd_normals_pca(g, stream=stream)   # warm
+        params = pd.pd_mlp_init(0, stream=stream)
+        pd.pd_mlp_forward(params, feat, stream=stream)
+        torch.cuda.synchronize()
+        t = {"normals_pca_ms": [], "mlp_forward_ms": []}
+        for _ in range(max(1, args.steps)):
+            for key, fn in (("normals_pca_ms", lambda: pd.pd_normals_pca(g, stream=stream)),
+                            ("mlp_forward_ms", lambda: pd.pd_mlp_forward(params, feat,
+                                                                         stream=stream))):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t[key].append(e0.elapsed_time(e1))
+        g.free()
+        fw = statistics.median(t["mlp_forward_ms"]) / 1e3
+        print(json.dumps({"normals_only": True, "n": n,
+                          "normals_pca_ms": statistics.median(t["normals_pca_ms"]),
+                          "mlp_forward_ms": fw * 1e3,
+                          "mlp_tflops": n * 2 * (48 * 64 + 64 * 64 + 64 * 3) / fw / 1e12,
+                          "mlp_gbs": n * (96 + 16) / fw / 1e9}))
+        return
+
     if args.knn_only:
         for _ in range(max(1, args.steps)):
             g = pd.Grid(ctx, xyz_dev, stream=stream)
@@ -495,6 +526,8 @@ def main(argv=None):
     ap.add_argument("--serve-pool", type=int, default=12)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
+    ap.add_argument("--normals-only", action="store_true",
+                    help="time the 16-NN/PCA pass and the network forward on the workload scan")
     ap.add_argument("--knn-only", action="store_true",
                     help="profiling aid: build the grid and run one full kNN/cost pass")
     args = ap.parse_args(argv)
