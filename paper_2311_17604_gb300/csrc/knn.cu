@@ -67,6 +67,25 @@ struct TopList<S, false> {
             if (i == r) v = d[i];
         return v;
     }
+    __device__ __forceinline__ u64 dist(int i) const { return d[i]; }
+    __device__ __forceinline__ int ident(int i) const { return id[i]; }
+    __device__ __forceinline__ bool has(int i) const { return d[i] != ~0ull; }
+    // merge the list of lane (lane ^ off) into this lane's (active lanes only)
+    __device__ __forceinline__ void merge_xor(int off, bool active) {
+        u64 od[S];
+        int oj[S], oo[S];
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            od[i] = __shfl_xor_sync(0xffffffffu, d[i], off);
+            oj[i] = __shfl_xor_sync(0xffffffffu, id[i], off);
+            oo[i] = __shfl_xor_sync(0xffffffffu, tie(i), off);
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < S; i++)
+                if (od[i] != ~0ull && beats_last(od[i], oj[i], oo[i])) insert(od[i], oj[i], oo[i]);
+        }
+    }
 };
 
 template <int S>
@@ -110,6 +129,113 @@ struct TopList<S, true> {
         for (int i = 1; i < S; i++)
             if (i == r) v = d[i];
         return v;
+    }
+    __device__ __forceinline__ u64 dist(int i) const { return d[i]; }
+    __device__ __forceinline__ int ident(int i) const { return id[i]; }
+    __device__ __forceinline__ bool has(int i) const { return d[i] != ~0ull; }
+    // merge the list of lane (lane ^ off) into this lane's (active lanes only)
+    __device__ __forceinline__ void merge_xor(int off, bool active) {
+        u64 od[S];
+        int oj[S], oo[S];
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            od[i] = __shfl_xor_sync(0xffffffffu, d[i], off);
+            oj[i] = __shfl_xor_sync(0xffffffffu, id[i], off);
+            oo[i] = __shfl_xor_sync(0xffffffffu, tie(i), off);
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < S; i++)
+                if (od[i] != ~0ull && beats_last(od[i], oj[i], oo[i])) insert(od[i], oj[i], oo[i]);
+        }
+    }
+};
+
+
+// The same lists when every squared distance of the search level is below
+// 2^32: one 64-bit key (d^2 << 32 | tie) per entry, so that a compare-exchange
+// stage is one 64-bit compare and select.  The order is the same as above
+// ((d^2, tie) lexicographic), so results are identical.  W = false: the tie is
+// the Morton position, which is also the neighbour; W = true: the tie is the
+// input index and the Morton position is kept beside it.
+template <int S, bool W>
+struct TopPack {
+    u64 key[S];
+    int pid[W ? S : 1];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < S; i++) key[i] = ~0ull;
+        if (W) {
+#pragma unroll
+            for (int i = 0; i < S; i++) pid[W ? i : 0] = 0x7fffffff;
+        }
+    }
+    __device__ __forceinline__ static u64 pack(u64 dd, int j, int o) {
+        return (dd << 32) | (uint32_t)(W ? o : j);
+    }
+    __device__ __forceinline__ int tie(int i) const { return (int)(uint32_t)key[i]; }
+    __device__ __forceinline__ bool beats_last(u64 dd, int j, int o) const {
+        return pack(dd, j, o) < key[S - 1];
+    }
+    __device__ __forceinline__ void insert(u64 dd, int j, int o) {
+        key[S - 1] = pack(dd, j, o);
+        if (W) pid[W ? S - 1 : 0] = j;
+#pragma unroll
+        for (int i = S - 1; i > 0; i--) {
+            u64 a = key[i], b = key[i - 1];
+            bool sw = a < b;
+            key[i - 1] = sw ? a : b;
+            key[i] = sw ? b : a;
+            if (W) {
+                int x = pid[W ? i : 0], y = pid[W ? i - 1 : 0];
+                pid[W ? i - 1 : 0] = sw ? x : y;
+                pid[W ? i : 0] = sw ? y : x;
+            }
+        }
+    }
+    __device__ __forceinline__ bool has(int i) const { return key[i] != ~0ull; }
+    __device__ __forceinline__ u64 dist(int i) const {
+        return key[i] == ~0ull ? ~0ull : (key[i] >> 32);
+    }
+    __device__ __forceinline__ int ident(int i) const {
+        return W ? pid[W ? i : 0] : (int)(uint32_t)key[i];
+    }
+    __device__ __forceinline__ u64 at(int r) const {
+        u64 v = key[0];
+#pragma unroll
+        for (int i = 1; i < S; i++)
+            if (i == r) v = key[i];
+        return v == ~0ull ? ~0ull : (v >> 32);
+    }
+    __device__ __forceinline__ void merge_xor(int off, bool active) {
+        u64 ok[S];
+        int op[W ? S : 1];
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            ok[i] = __shfl_xor_sync(0xffffffffu, key[i], off);
+            if (W) op[W ? i : 0] = __shfl_xor_sync(0xffffffffu, pid[W ? i : 0], off);
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < S; i++) {
+                if (ok[i] != ~0ull && ok[i] < key[S - 1]) {
+                    key[S - 1] = ok[i];
+                    if (W) pid[W ? S - 1 : 0] = op[W ? i : 0];
+#pragma unroll
+                    for (int t = S - 1; t > 0; t--) {
+                        u64 a = key[t], b = key[t - 1];
+                        bool sw = a < b;
+                        key[t - 1] = sw ? a : b;
+                        key[t] = sw ? b : a;
+                        if (W) {
+                            int x = pid[W ? t : 0], y = pid[W ? t - 1 : 0];
+                            pid[W ? t - 1 : 0] = sw ? x : y;
+                            pid[W ? t : 0] = sw ? y : x;
+                        }
+                    }
+                }
+            }
+        }
     }
 };
 
@@ -175,25 +301,25 @@ __device__ inline double nbr_weight(const KnnArgs& a, int q, int j) {
     return 1.0;
 }
 
-template <int S, bool W>
-__device__ inline double cost_sum(const KnnArgs& a, int q, const TopList<S, W>& top, int k) {
+template <int S, class TL>
+__device__ inline double cost_sum(const KnnArgs& a, int q, const TL& top, int k) {
     double c = 0.0;
 #pragma unroll
     for (int i = 0; i < S; i++) {
-        if (i < k && top.d[i] != ~0ull) {
-            double w = nbr_weight(a, q, top.id[i]);
-            c = __dadd_rn(c, __ddiv_rn(w, (double)top.d[i]));
+        if (i < k && top.has(i)) {
+            double w = nbr_weight(a, q, top.ident(i));
+            c = __dadd_rn(c, __ddiv_rn(w, (double)top.dist(i)));
         }
     }
     return c;
 }
 
 // Stream one range [b, e) of Morton positions against every lane's query.
-template <int S, int FILT, bool W, typename D>
+template <int S, int FILT, bool W, class TL, typename D>
 __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, uint32_t b,
                                            uint32_t e, int q, int4 qp, bool todo, u64 tp, int ti,
-                                           TopList<S, W>& top, int4* sp, u64* sk, int* so,
-                                           int lane, int sub, int lpq) {
+                                           TL& top, int4* sp, u64* sk, int* so, int lane, int sub,
+                                           int lpq) {
     for (uint32_t c = b; c < e; c += 32) {
         uint32_t j = c + lane;
         int4 v = make_int4(0, 0, 0, -1);
@@ -208,7 +334,6 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
         __syncwarp();
         int m = (int)min(32u, e - c);
         if (todo) {
-            D worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
             for (int t = sub; t < m; t += lpq) {
                 int4 cv = sp[t];
                 if (cv.w < 0 || cv.w == q) continue;
@@ -223,13 +348,103 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
                     dd = (D)((long long)dx * dx) + (D)((long long)dy * dy) + (D)((long long)dz * dz);
                 }
                 int co = W ? so[t] : cv.w;
-                if (dd < worst || (dd == worst && co < top.tie(S - 1))) {
-                    top.insert((u64)dd, cv.w, co);
-                    worst = top.d[S - 1] > (u64)(D)~(D)0 ? (D)~(D)0 : (D)top.d[S - 1];
-                }
+                if (top.beats_last((u64)dd, cv.w, co)) top.insert((u64)dd, cv.w, co);
             }
         }
         __syncwarp();
+    }
+}
+
+// Results of a query whose list is exact (one lane per query).
+template <int S, int FILT, bool W, class TL>
+__device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& top) {
+    int found = 0;
+#pragma unroll
+    for (int i = 0; i < S; i++) found += top.has(i);
+    if (FILT == FILT_NONE) {
+        if (a.density_k1) {
+            u64 d0 = top.dist(0);
+            int shell = 0;
+#pragma unroll
+            for (int i = 0; i < S; i++) {
+                bool in = d0 != ~0ull && top.dist(i) == d0;
+                shell += in;
+                a.nbr[(int64_t)q * S + i] = in ? top.ident(i) : -1;
+            }
+            a.prim_out[q] = key_prim_d2(d0);
+            a.rk2_out[q] = d0;
+            a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0));
+            if (a.cost_out) a.cost_out[q] = d0 == ~0ull ? 0.0 : __ddiv_rn(1.0, (double)d0);
+        } else {
+            int k = a.k;
+#pragma unroll
+            for (int i = 0; i < S; i++) a.nbr[(int64_t)q * S + i] = top.has(i) ? top.ident(i) : -1;
+            double c = cost_sum<S>(a, q, top, k);
+            a.prim_out[q] = key_prim_cost(c);
+            u64 dk = top.at(k - 1);
+            a.rk2_out[q] = dk;
+            bool tie = found > k && top.at(k) == dk;
+            a.flg_out[q] = (uint8_t)(tie ? 1 : 0);
+            if (a.hz_out) a.hz_out[q] = top.dist(S - 1);
+            if (a.cost_out) a.cost_out[q] = c;
+        }
+    } else if (FILT == FILT_BELOW_SELF) {
+        if (a.density_k1) {
+            a.fprim_out[q] = key_prim_d2(top.dist(0));
+        } else {
+            a.fprim_out[q] = key_prim_cost(cost_sum<S>(a, q, top, a.k));
+        }
+    } else {
+        a.lam_out[q] = top.at(a.k - 1);
+    }
+}
+
+// One search level for the warp: scan the resolved 3x3x3 ranges, merge each
+// query's partial lists, and finish the queries whose R-th distance is
+// closer than the searched cube's faces.  PACK: every range of this level
+// has squared distances below 2^32 (packed lists, 32-bit distances).
+template <int S, int FILT, bool W, class TL, bool PACK>
+__device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, int L, int R,
+                                          int q, int4 qp, int ux, int uy, int uz, bool& todo,
+                                          u64 tp, int ti, int lane, int sub, int lpq, int rt,
+                                          uint32_t rb, uint32_t re, int rl, int bx, int by,
+                                          int bz, int cx, int cy, int cz, int4* sp, u64* sk,
+                                          int* so, unsigned long long& wpairs) {
+    TL top;
+    top.init();
+    for (int r = 0; r < 27; r++) {
+        int tr = __shfl_sync(FULLM, rt, r);
+        if (!tr) continue;
+        uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
+        int lv = __shfl_sync(FULLM, rl, r);
+        int bxr = __shfl_sync(FULLM, bx, r), byr = __shfl_sync(FULLM, by, r),
+            bzr = __shfl_sync(FULLM, bz, r);
+        bool skip = true;
+        if (todo) {
+            u64 bound = top.at(R - 1);
+            skip = bound != ~0ull && box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift) > bound;
+        }
+        if (__all_sync(FULLM, skip)) continue;
+        if (a.pairs_out) {  // warp-uniform count of the pairs this range costs
+            int nqt = __popc(__ballot_sync(FULLM, todo && sub == 0));
+            wpairs += (unsigned long long)(e - b) * (unsigned long long)nqt;
+        }
+        if (PACK || lv + g.shift <= 13)
+            scan_range<S, FILT, W, TL, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, sp, sk, so,
+                                                 lane, sub, lpq);
+        else
+            scan_range<S, FILT, W, TL, u64>(g, a, b, e, q, qp, todo, tp, ti, top, sp, sk, so, lane,
+                                            sub, lpq);
+    }
+    // merge the partial lists of each query's lanes (butterfly)
+    for (int off = lpq >> 1; off >= 1; off >>= 1) top.merge_xor(off, todo);
+    if (todo) {
+        u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
+        u64 bound = top.at(R - 1);
+        if (gg == ~0ull || bound < gg) {
+            todo = false;
+            if (sub == 0) write_result<S, FILT, W>(a, q, top);
+        }
     }
 }
 
@@ -281,8 +496,6 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
     // searches: all S stored neighbours exact (the k+b neighbour buffer, so a
     // removal can be absorbed without a new search); filtered searches: k.
     const int R = FILT == FILT_NONE ? (a.density_k1 ? 1 : S) : a.k;
-    TopList<S, W> top;
-    top.init();
     bool todo = q >= 0;
     unsigned long long wpairs = 0;
     while (__any_sync(FULLM, todo)) {
@@ -306,99 +519,18 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
             by = (cy + dy) >> (rl - L);
             bz = (cz + dz) >> (rl - L);
         }
-        for (int r = 0; r < 27; r++) {
-            int tr = __shfl_sync(FULLM, rt, r);
-            if (!tr) continue;
-            uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
-            int lv = __shfl_sync(FULLM, rl, r);
-            int bxr = __shfl_sync(FULLM, bx, r), byr = __shfl_sync(FULLM, by, r),
-                bzr = __shfl_sync(FULLM, bz, r);
-            bool skip = true;
-            if (todo) {
-                u64 bound = top.at(R - 1);
-                skip = bound != ~0ull && box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift) > bound;
-            }
-            if (__all_sync(FULLM, skip)) continue;
-            if (a.pairs_out) {  // warp-uniform count of the pairs this range costs
-                int nqt = __popc(__ballot_sync(FULLM, todo && sub == 0));
-                wpairs += (unsigned long long)(e - b) * (unsigned long long)nqt;
-            }
-            if (lv + g.shift <= 13)
-                scan_range<S, FILT, W, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w],
-                                                 s_k[w], s_o[w], lane, sub, lpq);
-            else
-                scan_range<S, FILT, W, u64>(g, a, b, e, q, qp, todo, tp, ti, top, s_p[w], s_k[w],
-                                            s_o[w], lane, sub, lpq);
-        }
-        // merge the partial lists of each query's lanes (butterfly)
-        for (int off = lpq >> 1; off >= 1; off >>= 1) {
-            u64 od[S];
-            int oj[S], oo[S];
-#pragma unroll
-            for (int i = 0; i < S; i++) {
-                od[i] = __shfl_xor_sync(FULLM, top.d[i], off);
-                oj[i] = __shfl_xor_sync(FULLM, top.id[i], off);
-                oo[i] = W ? __shfl_xor_sync(FULLM, top.tie(i), off) : oj[i];
-            }
-            if (todo) {
-#pragma unroll
-                for (int i = 0; i < S; i++)
-                    if (od[i] != ~0ull && top.beats_last(od[i], oj[i], oo[i]))
-                        top.insert(od[i], oj[i], oo[i]);
-            }
-        }
-        if (todo) {
-            u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
-            u64 bound = top.at(R - 1);
-            if (gg == ~0ull || bound < gg) {
-                todo = false;
-                if (sub == 0) {  // one lane per query writes the result
-                int found = 0;
-#pragma unroll
-                for (int i = 0; i < S; i++) found += top.d[i] != ~0ull;
-                if (FILT == FILT_NONE) {
-                    if (a.density_k1) {
-                        u64 d0 = top.d[0];
-                        int shell = 0;
-#pragma unroll
-                        for (int i = 0; i < S; i++) {
-                            bool in = d0 != ~0ull && top.d[i] == d0;
-                            shell += in;
-                            a.nbr[(int64_t)q * S + i] = in ? top.id[i] : -1;
-                        }
-                        a.prim_out[q] = key_prim_d2(d0);
-                        a.rk2_out[q] = d0;
-                        a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0));
-                        if (a.cost_out)
-                            a.cost_out[q] = d0 == ~0ull ? 0.0 : __ddiv_rn(1.0, (double)d0);
-                    } else {
-                        int k = a.k;
-#pragma unroll
-                        for (int i = 0; i < S; i++)
-                            a.nbr[(int64_t)q * S + i] = top.d[i] != ~0ull ? top.id[i] : -1;
-                        double c = cost_sum<S, W>(a, q, top, k);
-                        a.prim_out[q] = key_prim_cost(c);
-                        u64 dk = top.at(k - 1);
-                        a.rk2_out[q] = dk;
-                        bool tie = found > k && top.at(k) == dk;
-                        a.flg_out[q] = (uint8_t)(tie ? 1 : 0);
-                        if (a.hz_out) a.hz_out[q] = top.d[S - 1];
-                        if (a.cost_out) a.cost_out[q] = c;
-                    }
-                } else if (FILT == FILT_BELOW_SELF) {
-                    if (a.density_k1) {
-                        a.fprim_out[q] = key_prim_d2(top.d[0]);
-                    } else {
-                        a.fprim_out[q] = key_prim_cost(cost_sum<S, W>(a, q, top, a.k));
-                    }
-                } else {
-                    a.lam_out[q] = top.at(a.k - 1);
-                }
-                }
-            } else {
-                top.init();
-            }
-        }
+        // 32-bit distances and packed lists when every range of this level is
+        // within 3 cells of 2^13 mm (squared distances < 3 * 24576^2 < 2^32)
+        bool pack = __all_sync(FULLM, !rt || rl + g.shift <= 13);
+        if (pack)
+            knn_level<S, FILT, W, TopPack<S, W>, true>(g, a, L, R, q, qp, ux, uy, uz, todo, tp, ti,
+                                                       lane, sub, lpq, rt, rb, re, rl, bx, by, bz,
+                                                       cx, cy, cz, s_p[w], s_k[w], s_o[w], wpairs);
+        else
+            knn_level<S, FILT, W, TopList<S, W>, false>(g, a, L, R, q, qp, ux, uy, uz, todo, tp,
+                                                        ti, lane, sub, lpq, rt, rb, re, rl, bx, by,
+                                                        bz, cx, cy, cz, s_p[w], s_k[w], s_o[w],
+                                                        wpairs);
         L++;
     }
     if (a.pairs_out && lane == 0 && wpairs) atomicAdd(a.pairs_out, wpairs);
