@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(BW_THREADS)
     mlp_backward_kernel(const float* __restrict__ prm, const uint16_t* __restrict__ feat,
                         const int* __restrict__ rows, const float* __restrict__ labels, int64_t n,
                         const float* __restrict__ h1s, const float* __restrict__ h2s,
-                        const float* __restrict__ raw, float* grad, float* loss) {
+                        const float* __restrict__ raw, float* __restrict__ part) {
     __shared__ float sx[BW_ROWS][NF];
     __shared__ float sh1[BW_ROWS][NH];
     __shared__ float sh2[BW_ROWS][NH];
@@ -451,15 +451,29 @@ __global__ void __launch_bounds__(BW_THREADS)
             acc[jj] += v;
         }
     }
+    // this block's partial sums; grad_reduce_kernel adds the blocks in a fixed
+    // order, so the gradient is the same bit for bit on every run
+    float* mine = part + (int64_t)blockIdx.x * (N_PARAMS + 1);
 #pragma unroll
     for (int jj = 0; jj < BW_PER_THREAD; jj++) {
         int i = tid + BW_THREADS * jj;
-        if (i < N_PARAMS && acc[jj] != 0.f) atomicAdd(&grad[i], acc[jj]);
+        if (i < N_PARAMS) mine[i] = acc[jj];
     }
     if (tid < 32) {
         for (int off = 16; off; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-        if (tid == 0 && lsum != 0.f) atomicAdd(loss, lsum * inv_n);
+        if (tid == 0) mine[N_PARAMS] = lsum * inv_n;
     }
+}
+
+// grad[i] (and the loss, entry N_PARAMS) = sum of the blocks' partials in block order.
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int nblocks, float* grad,
+                                   float* loss) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > N_PARAMS) return;
+    float v = 0.f;
+    for (int b = 0; b < nblocks; b++) v += part[(int64_t)b * (N_PARAMS + 1) + i];
+    if (i < N_PARAMS) grad[i] = v;
+    else *loss = v;
 }
 
 // ------------------------------------------------------------------ Adam, init, sampling
@@ -561,18 +575,24 @@ cudaError_t launch_mlp_forward(const float* prm, const uint16_t* feat, const int
     return cudaGetLastError();
 }
 
+int64_t mlp_backward_part_floats() { return (int64_t)sm_count() * (N_PARAMS + 1); }
+
 cudaError_t launch_mlp_backward(const float* prm, const uint16_t* feat, const int* rows,
                                 const float* labels, int64_t n, const float* h1s,
                                 const float* h2s, const float* raw, float* grad, float* loss,
-                                cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(grad, 0, N_PARAMS * sizeof(float), st);
-    if (!e) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
-    if (e || n <= 0) return e;
+                                float* part, cudaStream_t st) {
+    if (n <= 0) {
+        cudaError_t e = cudaMemsetAsync(grad, 0, N_PARAMS * sizeof(float), st);
+        if (!e) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+        return e;
+    }
     int64_t tiles = (n + BW_ROWS - 1) / BW_ROWS;
     int64_t sms = sm_count();
     int64_t blocks = tiles < sms ? tiles : sms;
     mlp_backward_kernel<<<(unsigned)blocks, BW_THREADS, 0, st>>>(prm, feat, rows, labels, n, h1s,
-                                                                 h2s, raw, grad, loss);
+                                                                 h2s, raw, part);
+    note_launch();
+    grad_reduce_kernel<<<(N_PARAMS + 1 + 255) / 256, 256, 0, st>>>(part, (int)blocks, grad, loss);
     note_launch();
     return cudaGetLastError();
 }
@@ -663,10 +683,10 @@ extern "C" int pd_mlp_forward(const float* params_dev, const uint16_t* feat_dev,
 // Forward with stored activations and backward over `rows` (NULL = 0..n-1).
 static int grad_pass(pd_ctx* ctx, const float* prm, const uint16_t* feat, const int* rows,
                      const float* labels, int64_t n, float* h1s, float* h2s, float* raw,
-                     float* grad, float* loss, cudaStream_t st) {
+                     float* grad, float* loss, float* part, cudaStream_t st) {
     int rc = PD_OK;
     NCK(launch_mlp_forward(prm, feat, rows, n, nullptr, nullptr, h1s, h2s, raw, st));
-    NCK(launch_mlp_backward(prm, feat, rows, labels, n, h1s, h2s, raw, grad, loss, st));
+    NCK(launch_mlp_backward(prm, feat, rows, labels, n, h1s, h2s, raw, grad, loss, part, st));
 done:
     return rc;
 }
@@ -678,17 +698,19 @@ extern "C" int pd_mlp_grad(pd_ctx* ctx, const float* params_dev, const uint16_t*
         return PD_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int rc = PD_OK;
-    float *h1s = nullptr, *h2s = nullptr, *raw = nullptr;
+    float *h1s = nullptr, *h2s = nullptr, *raw = nullptr, *part = nullptr;
     NALLOC(h1s, float, n * NH);
     NALLOC(h2s, float, n * NH);
     NALLOC(raw, float, n * 3);
+    NALLOC(part, float, mlp_backward_part_floats());
     rc = grad_pass(ctx, params_dev, feat_dev, nullptr, labels_dev, n, h1s, h2s, raw, grad_dev,
-                   loss_dev, st);
+                   loss_dev, part, st);
     if (!rc) NCK(cudaStreamSynchronize(st));
 done:
     api_free(ctx, h1s, st);
     api_free(ctx, h2s, st);
     api_free(ctx, raw, st);
+    api_free(ctx, part, st);
     return rc;
 }
 
@@ -704,6 +726,7 @@ extern "C" int pd_mlp_train(pd_ctx* ctx, float* params_dev, float* adam_dev, int
     int b = tp->batch;
     int *pool = nullptr, *cnt = nullptr, *rows = nullptr;
     float *h1s = nullptr, *h2s = nullptr, *raw = nullptr, *grad = nullptr, *lossbuf = nullptr;
+    float* part = nullptr;
     int npool = 0;
     NALLOC(pool, int, n);
     NALLOC(cnt, int, 1);
@@ -713,6 +736,7 @@ extern "C" int pd_mlp_train(pd_ctx* ctx, float* params_dev, float* adam_dev, int
     NALLOC(raw, float, (int64_t)b * 3);
     NALLOC(grad, float, N_PARAMS);
     NALLOC(lossbuf, float, 1);
+    NALLOC(part, float, mlp_backward_part_floats());
     if (valid_dev) {
         Scratch s;
         struct Ctx {
@@ -744,13 +768,14 @@ extern "C" int pd_mlp_train(pd_ctx* ctx, float* params_dev, float* adam_dev, int
         int t = step0 + i + 1;
         NCK(launch_sample_rows(pool, npool, tp->seed, t, b, rows, st));
         float* lp = loss_dev ? loss_dev + i : lossbuf;
-        rc = grad_pass(ctx, params_dev, feat_dev, rows, labels_dev, b, h1s, h2s, raw, grad, lp, st);
+        rc = grad_pass(ctx, params_dev, feat_dev, rows, labels_dev, b, h1s, h2s, raw, grad, lp,
+                       part, st);
         if (rc) goto done;
         NCK(launch_adam(params_dev, adam_dev, adam_dev + N_PARAMS, grad, t, tp->lr, st));
     }
     NCK(cudaStreamSynchronize(st));
 done:
-    void* bufs[] = {pool, cnt, rows, h1s, h2s, raw, grad, lossbuf};
+    void* bufs[] = {pool, cnt, rows, h1s, h2s, raw, grad, lossbuf, part};
     for (void* p : bufs) api_free(ctx, p, st);
     return rc;
 }

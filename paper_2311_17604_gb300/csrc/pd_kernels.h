@@ -190,10 +190,13 @@ cudaError_t launch_features(const int4* pos, const int* nbr, int S, int64_t n, u
 cudaError_t launch_mlp_forward(const float* prm, const uint16_t* feat, const int* rows, int64_t n,
                                float* outn, float* onorm, float* h1s, float* h2s, float* raw,
                                cudaStream_t st);
+// Partials: mlp_backward_part_floats() floats of scratch; the gradient is
+// reduced over blocks in a fixed order (deterministic).
+int64_t mlp_backward_part_floats();
 cudaError_t launch_mlp_backward(const float* prm, const uint16_t* feat, const int* rows,
                                 const float* labels, int64_t n, const float* h1s,
                                 const float* h2s, const float* raw, float* grad, float* loss,
-                                cudaStream_t st);
+                                float* part, cudaStream_t st);
 cudaError_t launch_adam(float* prm, float* m, float* v, const float* grad, int t, float lr,
                         cudaStream_t st);
 cudaError_t launch_mlp_init(float* prm, u64 seed, cudaStream_t st);

@@ -351,9 +351,10 @@ __device__ inline int cover_level(const GridView& g, int ux, int uy, int uz, u64
 struct DangerSmem {
     int c_j[DG_WARPS][DG_CAP];
     u64 c_d[DG_WARPS][DG_CAP];
-    int4 st_p[DG_WARPS][32];
-    u64 st_k[DG_WARPS][32];
+    u64 st_d[DG_WARPS][32];  // staged points within the batch's farthest candidate:
+    u64 st_k[DG_WARPS][32];  // d^2 to the source, key, input index, Morton position
     int st_o[DG_WARPS][32];
+    int st_j[DG_WARPS][32];
 };
 
 __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ prim,
@@ -364,9 +365,10 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
                            const int* __restrict__ ncs, DangerSmem& sm, int w, int lane) {
     int(&c_j)[DG_WARPS][DG_CAP] = sm.c_j;
     u64(&c_d)[DG_WARPS][DG_CAP] = sm.c_d;
-    int4(&st_p)[DG_WARPS][32] = sm.st_p;
+    u64(&st_d)[DG_WARPS][32] = sm.st_d;
     u64(&st_k)[DG_WARPS][32] = sm.st_k;
     int(&st_o)[DG_WARPS][32] = sm.st_o;
+    int(&st_j)[DG_WARPS][32] = sm.st_j;
     __syncwarp();
     int4 xp = g.pos[x];
     u64 px = prim[x];
@@ -508,24 +510,37 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
             if (__shfl_sync(FULLM, rbox, r) > dmax) continue;
             uint32_t b = __shfl_sync(FULLM, rb, r), e = __shfl_sync(FULLM, re, r);
             for (uint32_t c = b; c < e; c += 32) {
+                // each lane loads one point and its distance to x; only points
+                // within the batch's farthest open candidate can shield, and
+                // they are compacted into the staging buffer
                 uint32_t j = c + lane;
-                int4 v = make_int4(0, 0, 0, -1);
+                bool near = false;
+                u64 d2 = 0, ky = 0;
+                int oy = 0;
                 if (j < e && (int)j != x && alive[j]) {
-                    v = g.pos[j];
-                    st_k[w][lane] = prim[j];
-                    st_o[w][lane] = v.w;
-                    v.w = (int)j;
+                    int4 v = g.pos[j];
+                    long long ddx = v.x - xp.x, ddy = v.y - xp.y, ddz = v.z - xp.z;
+                    d2 = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
+                    near = d2 <= dmax;
+                    if (near) {
+                        ky = prim[j];
+                        oy = v.w;
+                    }
                 }
-                st_p[w][lane] = v;
+                unsigned nb = __ballot_sync(FULLM, near);
+                if (near) {
+                    int slot = __popc(nb & ((1u << lane) - 1u));
+                    st_d[w][slot] = d2;
+                    st_k[w][slot] = ky;
+                    st_o[w][slot] = oy;
+                    st_j[w][slot] = (int)j;
+                }
                 __syncwarp();
-                int mm = (int)min(32u, e - c);
+                int mm = __popc(nb);
                 if (!done) {
                     for (int tt = 0; tt < mm; tt++) {
-                        int4 y = st_p[w][tt];
-                        if (y.w < 0 || y.w == p) continue;
-                        long long ddx = y.x - xp.x, ddy = y.y - xp.y, ddz = y.z - xp.z;
-                        u64 d2 = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
-                        if (d2 <= dp && key_gt(pp, ip, st_k[w][tt], st_o[w][tt])) {
+                        if (st_j[w][tt] == p) continue;
+                        if (st_d[w][tt] <= dp && key_gt(pp, ip, st_k[w][tt], st_o[w][tt])) {
                             if (++cnt >= k) {
                                 done = true;
                                 break;
@@ -764,7 +779,7 @@ cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* pr
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
                                 int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
-    danger_kernel<<<152 * 8, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
+    danger_kernel<<<152 * 10, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
                                                      &rd->cap_over, csorted, &rd->ncs); note_launch();

@@ -160,6 +160,20 @@ def test_adam_steps_match_oracle(pd, ctx):
     assert close.mean() > 0.98
 
 
+def test_training_is_reproducible(pd, ctx):
+    xyz = _room(9, 160, 50).xyz
+    feat, pca, valid = _gpu_features(pd, ctx, xyz)
+    runs = []
+    for _ in range(2):
+        tr = pd.MlpTrainer(seed=5)
+        losses = tr.train(ctx, feat, pca, valid, steps=20, batch=1000, lr=1e-3, seed=7)
+        runs.append((tr.params.clone(), losses.clone()))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+    g1 = pd.pd_mlp_grad(ctx, runs[0][0], feat, pca)[1]
+    g2 = pd.pd_mlp_grad(ctx, runs[0][0], feat, pca)[1]
+    assert torch.equal(g1, g2)
+
+
 def test_fallback_rules(pd, ctx):
     xyz = _room(8, 120, 40).xyz
     feat, pca, _ = _gpu_features(pd, ctx, xyz)
