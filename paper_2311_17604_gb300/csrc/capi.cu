@@ -122,6 +122,8 @@ struct pd_grid {
     u64* rk2;
     uint8_t* flg;
     u64* hz;  // k+b buffer horizon
+    int* glist;  // flagged searches: groups holding a flagged query, and their count
+    int* gcount;
     // small device scalars
     int* d_int;                  // [0] ngroups, [1..7] counters
     unsigned long long* d_u64;   // [0] counts
@@ -264,7 +266,8 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 // ============================================================ API: grid
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
-                    g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64};
+                    g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64, g->glist,
+                    g->gcount};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -659,7 +662,11 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
     a.rd = rd;
     if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
     if (filter == FILT_BELOW_TAU) a.lam_out = fout;
-    CK(launch_knn(view_of(g), a, g->st));
+    if (!g->glist) {  // groups never outnumber the points of the first build
+        ALLOC(g->glist, int, g->n);
+        ALLOC(g->gcount, int, 1);
+    }
+    CK(launch_knn_flagged(view_of(g), a, g->glist, g->gcount, g->st));
     return PD_OK;
 }
 

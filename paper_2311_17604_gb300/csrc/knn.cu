@@ -448,14 +448,10 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
     }
 }
 
+// One leaf group (<= 32 queries) for one warp.
 template <int S, int FILT, bool W>
-__global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs a) {
-    __shared__ int4 s_p[PD_WARPS][32];
-    __shared__ u64 s_k[PD_WARPS][32];
-    __shared__ int s_o[PD_WARPS][32];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int gid = blockIdx.x * PD_WARPS + w;
-    if (gid >= a.ngroups) return;
+__device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, int gid, int4* sp,
+                                          u64* sk, int* so, int lane) {
     int4 G = a.groups[gid];
     int cnt = G.y;
     int L = G.z;
@@ -525,25 +521,69 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
         if (pack)
             knn_level<S, FILT, W, TopPack<S, W>, true>(g, a, L, R, q, qp, ux, uy, uz, todo, tp, ti,
                                                        lane, sub, lpq, rt, rb, re, rl, bx, by, bz,
-                                                       cx, cy, cz, s_p[w], s_k[w], s_o[w], wpairs);
+                                                       cx, cy, cz, sp, sk, so, wpairs);
         else
             knn_level<S, FILT, W, TopList<S, W>, false>(g, a, L, R, q, qp, ux, uy, uz, todo, tp,
                                                         ti, lane, sub, lpq, rt, rb, re, rl, bx, by,
-                                                        bz, cx, cy, cz, s_p[w], s_k[w], s_o[w],
-                                                        wpairs);
+                                                        bz, cx, cy, cz, sp, sk, so, wpairs);
         L++;
     }
     if (a.pairs_out && lane == 0 && wpairs) atomicAdd(a.pairs_out, wpairs);
+}
+
+template <int S, int FILT, bool W, bool LIST>
+__global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs a) {
+    __shared__ int4 s_p[PD_WARPS][32];
+    __shared__ u64 s_k[PD_WARPS][32];
+    __shared__ int s_o[PD_WARPS][32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (LIST) {  // persistent over the listed groups
+        int ng = *a.gcount;
+        for (int t = blockIdx.x * PD_WARPS + w; t < ng; t += gridDim.x * PD_WARPS)
+            knn_group<S, FILT, W>(g, a, a.glist[t], s_p[w], s_k[w], s_o[w], lane);
+    } else {
+        int gid = blockIdx.x * PD_WARPS + w;
+        if (gid < a.ngroups) knn_group<S, FILT, W>(g, a, gid, s_p[w], s_k[w], s_o[w], lane);
+    }
+}
+
+// Append every group holding a flagged query to glist (one atomic per warp).
+__global__ void flagged_groups_kernel(const int4* __restrict__ groups, int ngroups,
+                                      const uint8_t* __restrict__ qflag, int* glist, int* gcount) {
+    int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (gid < ngroups) {
+        int4 G = groups[gid];
+        for (int i = 0; i < G.y && !any; i++) any = qflag[G.x + i] != 0;
+    }
+    unsigned bal = __ballot_sync(FULLM, any);
+    if (!bal) return;
+    int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(gcount, __popc(bal));
+    base = __shfl_sync(FULLM, base, 0);
+    if (any) glist[base + __popc(bal & ((1u << lane) - 1u))] = gid;
 }
 
 template <int S, int FILT>
 static cudaError_t launch_knn_t(const GridView& g, const KnnArgs& a, cudaStream_t st) {
     if (a.ngroups <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((a.ngroups + PD_WARPS - 1) / PD_WARPS);
-    if (a.term != 0)
-        knn_kernel<S, FILT, true><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
-    else
-        knn_kernel<S, FILT, false><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+    // list mode: a persistent grid (about 6 resident blocks per SM)
+    if (a.glist && blocks > 152u * 6u) blocks = 152u * 6u;
+    if (a.glist) {
+        if (a.term != 0)
+            knn_kernel<S, FILT, true, true><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+        else
+            knn_kernel<S, FILT, false, true><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+    } else if (FILT == FILT_NONE) {  // full passes: one warp per group
+        if (a.term != 0)
+            knn_kernel<S, FILT_NONE, true, false><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+        else
+            knn_kernel<S, FILT_NONE, false, false><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);
+    } else {
+        return cudaErrorInvalidValue;  // filtered searches always run over a group list
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -555,6 +595,20 @@ static cudaError_t launch_knn_s(const GridView& g, const KnnArgs& a, cudaStream_
         case FILT_BELOW_SELF: return launch_knn_t<S, FILT_BELOW_SELF>(g, a, st);
         default: return launch_knn_t<S, FILT_BELOW_TAU>(g, a, st);
     }
+}
+
+cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, int* gcount,
+                               cudaStream_t st) {
+    if (a.ngroups <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(gcount, 0, sizeof(int), st);
+    if (e) return e;
+    flagged_groups_kernel<<<(unsigned)((a.ngroups + 255) / 256), 256, 0, st>>>(
+        a.groups, a.ngroups, a.qflag, glist, gcount);
+    note_launch();
+    KnnArgs b = a;
+    b.glist = glist;
+    b.gcount = gcount;
+    return launch_knn(g, b, st);
 }
 
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st) {

@@ -109,7 +109,14 @@ struct KnnArgs {
     u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
     u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
     unsigned long long* pairs_out;  // optional: + (query, candidate) pairs scanned
+    const int* glist;         // group-list mode: process groups glist[0 .. *gcount)
+    const int* gcount;        //   (device count; a persistent grid walks the list)
 };
+// Flagged mode without a host read: list the groups that hold a flagged query
+// (a.qflag), then run the search over that list only.  glist: ngroups ints,
+// gcount: one int, both device scratch.
+cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, int* gcount,
+                               cudaStream_t st);
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
 // Internal neighbour-weight term: unit weights with equal distances ordered by
 // input index (the normals' 16-NN order).
