@@ -494,6 +494,19 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
     const int R = FILT == FILT_NONE ? (a.density_k1 ? 1 : S) : a.k;
     bool todo = q >= 0;
     unsigned long long wpairs = 0;
+    if (FILT == FILT_BELOW_TAU && a.hz_out) {
+        // a lambda search runs when fewer than k lower-key points are among a
+        // query's stored neighbours; every live point closer than its horizon
+        // hz is stored, so lambda >= hz: start at the first level whose cell
+        // edge reaches sqrt(hz) (smallest over the group's queries)
+        u64 h = q >= 0 ? a.hz_out[q] : ~0ull;
+        for (int off = 16; off; off >>= 1) {
+            u64 o = __shfl_xor_sync(FULLM, h, off);
+            h = o < h ? o : h;
+        }
+        if (h != ~0ull)
+            while (L < g.B && (1ull << (2 * (L + g.shift))) < h) L++;
+    }
     while (__any_sync(FULLM, todo)) {
         int sh = 3 * L;
         int cx = (int)compact3(c0 >> sh), cy = (int)compact3(c0 >> (sh + 1)),
