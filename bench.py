@@ -247,6 +247,9 @@ def run_batched(args, pd, torch, dev, stream):
         total += s.n
     ctx = pd.Context()
     kw = dict(k=1, term=pd.PD_TERM_COLOR, weight=0.3)
+    big = max(clouds, key=lambda c: int(c["xyz"].shape[0]))
+    leaf = args.leaf_max or pd.pd_autotune(ctx, big["xyz"], big["ratio"], rgb=big["rgb"],
+                                           sample=1_000_000, stream=stream, **kw)
     pd.pd_decimate_batch(ctx, clouds[:4], concurrency=4, stream=stream, **kw)   # warm
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -271,7 +274,7 @@ def run_batched(args, pd, torch, dev, stream):
     ctx.close()
     return {"workload": "%d room scans, sizes log-uniform 50k-5M (%d points), RGB, k=1 + 0.3 x "
                         "colour term, keep U[5%%, 50%%]" % (len(clouds), total),
-            "scans": len(clouds), "points": total, "slots": args.batch_slots,
+            "scans": len(clouds), "points": total, "slots": args.batch_slots, "leaf_max": leaf,
             "value": total / (batch_ms / 1e3), "unit": UNIT, "ms": batch_ms,
             "single_scan_loop": {"value": total / (single_ms / 1e3), "ms": single_ms},
             "speedup_vs_single": single_ms / batch_ms,
@@ -297,6 +300,8 @@ def run_serving(args, pd, torch, dev):
     g = pd.Grid(ctx, torch.from_numpy(tr_scan.xyz).to(dev))
     feat, pca, valid = pd.pd_normals_pca(g)
     g.free()
+    pd.MlpTrainer(seed=0).train(ctx, feat, pca, valid, steps=2, batch=256, lr=2e-3, seed=0)
+    torch.cuda.synchronize()   # first-call set-up outside the timed training
     trainer = pd.MlpTrainer(seed=0)
     t0 = time.perf_counter()
     losses = trainer.train(ctx, feat, pca, ((valid & pd.PD_NORMAL_PLANAR) != 0).to(torch.uint8),
@@ -312,6 +317,10 @@ def run_serving(args, pd, torch, dev):
     planar = ((valid & pd.PD_NORMAL_PLANAR) != 0).cpu().numpy()
     ang = onorm.angle(u.cpu().numpy()[planar], pca.cpu().numpy()[planar])
     ratio, k, w = 0.25, 4, 0.5
+    leaf = args.leaf_max or pd.pd_autotune(ctx, x0, ratio, k=k, term=pd.PD_TERM_ORIENT, weight=w,
+                                           normals=pd.pd_normals_mlp(ctx, trainer.params, feat,
+                                                                     pca),
+                                           sample=1_000_000)
     srv = pd.Server(ctx, slots=args.serve_slots, k=k, term=pd.PD_TERM_ORIENT, weight=w,
                     mlp_params=trainer.params, normals=True)
     # warm: one small request
@@ -348,7 +357,7 @@ def run_serving(args, pd, torch, dev):
                         "normals, keep %g%%" % (args.serve_requests, args.serve_rate,
                                                  len(pool), np.mean([n for _, n in pool]) / 1e6,
                                                  k, w, 100 * ratio),
-            "slots": args.serve_slots,
+            "slots": args.serve_slots, "leaf_max": leaf,
             "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat)},
             "queue_wait_ms": {"p50": _pct(qwait, 50), "p99": _pct(qwait, 99)},
             "throughput": pts / (span_ms / 1e3), "unit": UNIT,
@@ -381,7 +390,7 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
     L.pd__launch_count.restype = ctypes.c_longlong
 
     def step():
-        g = pd.Grid(ctx, xyz_dev, stream=stream)
+        g = pd.Grid(ctx, xyz_dev, leaf_max=args.leaf_max, stream=stream)
         keep = pd.pd_decimate_count(g, m, k=k, stream=stream)
         st = g.stats()
         g.free()
@@ -390,7 +399,7 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
     if args.normals_only:
         # profiling aid and measurement: 16-NN + features/PCA, then the network
         # forward over every point, each timed with CUDA events on `stream`
-        g = pd.Grid(ctx, xyz_dev, stream=stream)
+        g = pd.Grid(ctx, xyz_dev, leaf_max=args.leaf_max, stream=stream)
         feat, pca, valid = pd.pd_normals_pca(g, stream=stream)   # warm
         params = pd.pd_mlp_init(0, stream=stream)
         pd.pd_mlp_forward(params, feat, stream=stream)
@@ -420,13 +429,17 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
 
     if args.knn_only:
         for _ in range(max(1, args.steps)):
-            g = pd.Grid(ctx, xyz_dev, stream=stream)
+            g = pd.Grid(ctx, xyz_dev, leaf_max=args.leaf_max, stream=stream)
             pd.pd_knn_cost(g, k=k, stream=stream)
             g.free()
         torch.cuda.synchronize()
         print(json.dumps({"knn_only": True, "n": n, "k": k}))
         return
 
+    # leaf capacity: autotuned once on a 2M-point sample (outside the timed
+    # region), unless given
+    leaf = args.leaf_max or pd.pd_autotune(ctx, xyz_dev, wl["ratio"], k=k, sample=2_000_000,
+                                           stream=stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -492,7 +505,8 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64",
             "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": n, "m": m, "k": k,
+            "config": {"workload": wl["desc"], "n": n, "m": m, "k": k, "leaf_max": leaf,
+                       "leaf_max_from": "option" if args.leaf_max else "pd_autotune",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "256 MiB buffer written between timed steps; working set > L2"},
             "e2e": e2e,
@@ -517,6 +531,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="outdoor", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--leaf-max", type=int, default=0,
+                    help="octree leaf capacity, 4..32 (0: the library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-count", type=int, default=48)

@@ -71,7 +71,8 @@ typedef struct {
 } pd_allocator;
 
 typedef struct {
-    int32_t leaf_max;   /* most points per octree leaf cell, 4..32 (0 = 32) */
+    int32_t leaf_max;   /* most points per octree leaf cell, 4..32 (0 = the context's
+                           pd_autotune choice, else 32) */
     int32_t reserved[7];
 } pd_grid_params;
 
@@ -107,6 +108,8 @@ typedef struct {
     double ms_select;         /* of rules: on-device selection of the key threshold */
     double ms_danger;         /* of rules: k >= 2 danger-pair analysis */
     int64_t pairs_first;      /* (query, candidate) pairs the first pass scanned */
+    int32_t leaf_max;         /* the grid's octree leaf capacity */
+    int32_t reserved_stats;
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */
@@ -151,6 +154,24 @@ int pd_decimate_count(pd_grid* grid, const pd_cost_params* cp, int64_t m, uint8_
 /* Same with m = floor(ratio * n) computed in binary64 (lambda = m / |C|). */
 int pd_decimate_ratio(pd_grid* grid, const pd_cost_params* cp, double ratio, uint8_t* keep_dev,
                       void* stream);
+/*
+ * Autotuner for the octree leaf capacity (the cell size of the neighbour
+ * search).  The paper picks its voxel size by hand (section "Sub-sampling
+ * algorithm"); here the choice never changes a result (every search is exact
+ * at any leaf size), only the speed: large leaves favour the dense first
+ * pass, small ones the sparse searches of the removal rounds.  The call
+ * decimates the first min(n, sample) points (sample <= 0: all) of xyz_dev
+ * with cost cp and keep ratio `ratio` once per capacity in {12, 16, 24, 32}
+ * (after one untimed warm-up pass), times grid build + decimation with CUDA
+ * events on `stream`, and keeps the fastest.  The choice is stored in the
+ * context: pd_build_grid with leaf_max = 0 (or NULL params) uses it from then
+ * on.  *leaf_max_out (may be NULL) receives it.  Device scratch comes from
+ * the context's allocator; the stream is synchronised before returning.
+ */
+int pd_autotune(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t* rgb_dev, int64_t n,
+                const pd_cost_params* cp, double ratio, int64_t sample, void* stream,
+                int32_t* leaf_max_out);
+
 /* Counters of the last pd_decimate_* call on this grid. */
 int pd_grid_stats(const pd_grid* grid, pd_stats* out);
 

@@ -70,6 +70,7 @@ cudaError_t launch_take_f4(const int*, int64_t, const float4*, float4*, cudaStre
 struct pd_ctx {
     pd_allocator alloc;
     int has_alloc;
+    int tuned_leaf;  // leaf capacity chosen by pd_autotune (0: none yet)
     char err[512];
     std::mutex mu;  // guards err (batch slots report errors concurrently)
 };
@@ -237,6 +238,7 @@ extern "C" int pd_ctx_create(const pd_allocator* alloc, pd_ctx** out) {
     pd_ctx* c = new (std::nothrow) pd_ctx();
     if (!c) return PD_ENOMEM;
     c->has_alloc = 0;
+    c->tuned_leaf = 0;
     c->err[0] = 0;
     if (alloc && alloc->alloc && alloc->free) {
         c->alloc = *alloc;
@@ -287,13 +289,14 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
         if (ctx) set_err(ctx, "pd_build_grid: invalid argument%s (n = %lld)", "", (long long)n);
         return PD_EINVAL;
     }
-    int T = params && params->leaf_max ? params->leaf_max : 32;
+    int T = params && params->leaf_max ? params->leaf_max : (ctx->tuned_leaf ? ctx->tuned_leaf : 32);
     if (T < 4 || T > 32) {
         set_err(ctx, "pd_build_grid: leaf_max must be in [4, 32]%s (got %lld)", "", T);
         return PD_EINVAL;
     }
     pd_grid* g = new pd_grid();
     memset(&g->stats, 0, sizeof(g->stats));
+    g->stats.leaf_max = g->T;
     g->ctx = ctx;
     g->st = (cudaStream_t)stream;
     g->trace = getenv("PD_TRACE") != nullptr;
@@ -301,6 +304,7 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     g->n = n;
     g->ng = n;
     g->T = T;
+    g->stats.leaf_max = T;
     int rc = PD_OK;
     auto fail = [&](int code) {
         grid_release(g);
@@ -755,6 +759,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         return PD_EINVAL;
     }
     memset(&g->stats, 0, sizeof(g->stats));
+    g->stats.leaf_max = g->T;
     g->stats.n = g->n;
     g->stats.m = m;
     long long launches0 = g_launch_count;
@@ -1061,6 +1066,61 @@ extern "C" int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint
     ctx_free(ctx, keep, st);
     if (cudaStreamSynchronize(st) && !rc) rc = PD_ECUDA;
     return rc;
+}
+
+// ============================================================ API: autotune
+extern "C" int pd_autotune(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t* rgb_dev, int64_t n,
+                           const pd_cost_params* cp, double ratio, int64_t sample, void* stream,
+                           int32_t* leaf_max_out) {
+    if (!ctx || !xyz_dev || !cp || n < 1 || !(ratio >= 0.0 && ratio <= 1.0)) {
+        if (ctx) set_err(ctx, "pd_autotune: invalid argument%s", "", 0);
+        return PD_EINVAL;
+    }
+    static const int kLeaf[] = {12, 16, 24, 32};
+    const int64_t ns = sample > 0 && sample < n ? sample : n;
+    const int64_t m = (int64_t)((double)ns * ratio);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t* keep = (uint8_t*)ctx_alloc(ctx, (size_t)ns, st);
+    if (!keep) {
+        set_err(ctx, "pd_autotune: allocation failed%s", "", 0);
+        return PD_ENOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = PD_OK, best = 32;
+    float best_ms = 0.f;
+    // the first (untimed) pass takes the first-call costs out of the comparison
+    for (int t = -1; t < 4 && !rc; t++) {
+        pd_grid_params gp;
+        memset(&gp, 0, sizeof(gp));
+        gp.leaf_max = t < 0 ? 32 : kLeaf[t];
+        pd_grid* g = nullptr;
+        cudaEventRecord(e0, st);
+        rc = pd_build_grid(ctx, xyz_dev, rgb_dev, ns, &gp, stream, &g);
+        if (!rc) rc = pd_decimate_count(g, cp, m, keep, stream);
+        cudaEventRecord(e1, st);
+        if (g) pd_grid_free(g);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = PD_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (t >= 0 && (t == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = kLeaf[t];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx_free(ctx, keep, st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+    ctx->tuned_leaf = best;
+    if (leaf_max_out) *leaf_max_out = best;
+    return PD_OK;
 }
 
 // Internal diagnostics (not part of pd.h): copy one state array of the grid

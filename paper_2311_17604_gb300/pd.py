@@ -24,6 +24,7 @@ PD_STATIC_MAX_POINTS = 65536
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
             "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch",
+            "pd_autotune",
             # pd_normals.h
             "pd_normals_pca", "pd_mlp_init", "pd_mlp_forward", "pd_mlp_grad", "pd_mlp_train",
             "pd_normals_mlp",
@@ -69,7 +70,8 @@ class pd_stats(ctypes.Structure):
                 ("ms_knn_first", ctypes.c_double), ("q_first", ctypes.c_int64),
                 ("ms_knn_requery", ctypes.c_double), ("ms_rules", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("ms_select", ctypes.c_double),
-                ("ms_danger", ctypes.c_double), ("pairs_first", ctypes.c_int64)]
+                ("ms_danger", ctypes.c_double), ("pairs_first", ctypes.c_int64),
+                ("leaf_max", ctypes.c_int32), ("reserved_stats", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -130,6 +132,8 @@ def lib():
         L.pd_knn_cost_static.argtypes = [P, I64, ctypes.c_int, P, P, P]
         L.pd_decimate_batch.argtypes = [P, ctypes.POINTER(pd_scan_desc), ctypes.c_int,
                                         ctypes.POINTER(pd_cost_params), ctypes.c_int, P]
+        L.pd_autotune.argtypes = [P, P, P, I64, ctypes.POINTER(pd_cost_params), ctypes.c_double,
+                                  I64, P, ctypes.POINTER(ctypes.c_int32)]
         L.pd_normals_pca.argtypes = [P, P, P, P, P]
         L.pd_mlp_init.argtypes = [P, ctypes.c_uint64, P]
         L.pd_mlp_forward.argtypes = [P, P, I64, P, P, P]
@@ -327,6 +331,20 @@ def pd_decimate_host(ctx: Context, xyz: np.ndarray, m, k=1, term=PD_TERM_NONE, w
                                 int(m), _ptr(keep), _stream_ptr(stream), ctypes.byref(st))
     ctx.check(rc, "pd_decimate_host")
     return keep, st.as_dict()
+
+
+def pd_autotune(ctx: Context, xyz, ratio, k=1, term=PD_TERM_NONE, weight=0.0, normals=None,
+                rgb=None, sample=0, stream=None):
+    """Pick the octree leaf capacity for decimations like this one (timed on
+    the first `sample` points); stored in the context for later grids.
+    Returns the chosen capacity."""
+    xyz = xyz.contiguous()
+    out = ctypes.c_int32(0)
+    cp = cost_params(k, term, weight, normals)
+    rc = lib().pd_autotune(ctx.h, _ptr(xyz), _ptr(rgb), int(xyz.shape[0]), ctypes.byref(cp),
+                           float(ratio), int(sample), _stream_ptr(stream), ctypes.byref(out))
+    ctx.check(rc, "pd_autotune")
+    return int(out.value)
 
 
 def pd_knn_cost_static(xyz, k=1, cost=None, knn=None, stream=None):
