@@ -32,27 +32,14 @@ cudaError_t launch_sel_hist(const u64*, const uint8_t*, int64_t, const u64*, con
 cudaError_t launch_sel_compact(const u64*, const int4*, const uint8_t*, int64_t, const u64*,
                                const int*, int64_t, int, const uint32_t*, u64*, int*, int*,
                                cudaStream_t);
-cudaError_t launch_k1_cand(const u64*, const int4*, const uint8_t*, const int*, const uint8_t*,
-                           int64_t, int, u64, int, uint8_t*, int*, int*, int*, int*, cudaStream_t);
-cudaError_t launch_k1_slow(const GridView&, const u64*, const uint8_t*, const u64*, const int*,
-                           const int*, int, uint8_t*, int*, int*, cudaStream_t);
 cudaError_t launch_k1_fix(const int*, const int*, int, const int4*, const int*, int,
                           const uint8_t*, uint8_t*, int*, cudaStream_t);
-cudaError_t launch_kk_cand(const u64*, const int4*, const uint8_t*, const int*, const uint8_t*,
-                           int64_t, int, int, u64, int, uint8_t*, int*, int*, uint8_t*, uint8_t*,
-                           cudaStream_t);
-cudaError_t launch_kk_accept(const int*, const int*, int, const u64*, const u64*, uint8_t*, int*,
-                             int*, cudaStream_t);
-cudaError_t launch_danger(const GridView&, const int*, const int*, int, const u64*,
-                          const uint8_t*, const uint8_t*, uint8_t*, const u64*, int, int2*, int*,
-                          int, int*, unsigned long long*, cudaStream_t);
 cudaError_t launch_accept_above(const u64*, const int4*, const uint8_t*, int64_t, u64, int,
                                 uint8_t*, int*, int*, cudaStream_t);
 cudaError_t launch_pair_fix(const int2*, const int*, int, int, const uint8_t*, uint8_t*, int*,
                             cudaStream_t);
 cudaError_t launch_remove(const int*, const int*, int, uint8_t*, uint8_t*, uint8_t*,
                           unsigned long long*, cudaStream_t);
-cudaError_t launch_dirty(const uint8_t*, const int*, int64_t, int, int, uint8_t*, cudaStream_t);
 cudaError_t launch_keep(const int4*, const uint8_t*, int64_t, uint8_t*, cudaStream_t);
 cudaError_t launch_knn_out(const int4*, const double*, const int*, int64_t, int, int, double*,
                            int32_t*, cudaStream_t);

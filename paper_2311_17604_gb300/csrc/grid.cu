@@ -379,62 +379,6 @@ cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* 
     return cudaGetLastError();
 }
 
-// list groups: entry t starts a group when its (leaf, 32-chunk of the leaf
-// range) differs from entry t-1's.
-__global__ void list_head_kernel(GridView g, const int* __restrict__ list, int64_t len,
-                                 uint8_t* head, u64* chunk_id) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= len) return;
-    int s = list[t];
-    uint32_t b, e;
-    u64 id = ~0ull;
-    if (leaf_range(g, s, b, e)) id = ((u64)b << 32) | (((uint32_t)s - b) >> 5);
-    chunk_id[t] = id;
-}
-
-__global__ void list_head_flag_kernel(const u64* __restrict__ chunk_id, int64_t len,
-                                      uint8_t* head) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= len) return;
-    head[t] = (t == 0 || chunk_id[t] != chunk_id[t - 1]) ? 1 : 0;
-}
-
-__global__ void list_group_fill_kernel(GridView g, const int* __restrict__ list, int64_t len,
-                                       const int* __restrict__ heads, const int* nheads,
-                                       int4* groups) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int nh = *nheads;
-    if (t >= nh) return;
-    int off = heads[t];
-    int end = t + 1 < nh ? heads[t + 1] : (int)len;
-    int s = list[off];
-    groups[t] = make_int4(off, end - off, (int)g.leaf[s], 1);
-}
-
-cudaError_t launch_list_groups(const GridView& g, const int* list, int64_t len, int4* groups,
-                               int* ngroups, const Scratch& s, cudaStream_t st) {
-    if (len <= 0) return cudaMemsetAsync(ngroups, 0, sizeof(int), st);
-    uint8_t* head = (uint8_t*)s.get(len);
-    u64* cid = (u64*)s.get(len * sizeof(u64));
-    int* heads = (int*)s.get(len * sizeof(int));
-    cudaError_t e = (head && cid && heads) ? cudaSuccess : cudaErrorMemoryAllocation;
-    unsigned nb = (unsigned)((len + 255) / 256);
-    if (!e) {
-        list_head_kernel<<<nb, 256, 0, st>>>(g, list, len, head, cid); note_launch();
-        list_head_flag_kernel<<<nb, 256, 0, st>>>(cid, len, head); note_launch();
-        e = cudaGetLastError();
-    }
-    if (!e) e = stable_compact(head, len, heads, ngroups, s, st);
-    if (!e) {
-        list_group_fill_kernel<<<nb, 256, 0, st>>>(g, list, len, heads, ngroups, groups); note_launch();
-        e = cudaGetLastError();
-    }
-    s.put(heads);
-    s.put(cid);
-    s.put(head);
-    return e;
-}
-
 // ------------------------------------------------------------------ compaction
 __global__ void compact_count_kernel(const uint8_t* __restrict__ flag, int64_t n,
                                      uint32_t* counts) {

@@ -42,10 +42,6 @@ cudaError_t launch_node_insert(const u64* code, const uint8_t* leaf, int64_t n, 
 // Groups of <= 32 points of one leaf, for every point (full mode).
 cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* ngroups,
                                cudaStream_t st);
-// Groups over an ordered list of Morton positions: consecutive entries of the
-// same leaf chunk (32 positions of the leaf range) form one group.
-cudaError_t launch_list_groups(const GridView& g, const int* list, int64_t len, int4* groups,
-                               int* ngroups, const Scratch& s, cudaStream_t st);
 // Stable compaction: out = ascending s with flag[s] != 0; *count on device.
 cudaError_t stable_compact(const uint8_t* flag, int64_t n, int* out, int* count,
                            const Scratch& s, cudaStream_t st);
@@ -140,10 +136,6 @@ cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* a
                             const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
                             RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
                             cudaStream_t st);
-cudaError_t round_launch_kk_cand(const u64* prim, const int4* pos, const uint8_t* alive,
-                                 const int* nbr, const uint8_t* flg, int64_t n, int S, int k,
-                                 RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
-                                 uint8_t* dg_flag, int* src, cudaStream_t st);
 cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
                                    int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
                                    cudaStream_t st);

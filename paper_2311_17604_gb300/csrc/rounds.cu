@@ -134,92 +134,6 @@ __global__ void sel_compact_kernel(const u64* __restrict__ prim, const int4* __r
     }
 }
 
-// ------------------------------------------------------------------ k = 1 rule
-// Candidate test for k = 1: key >= tau and (A).  Shell members are the
-// stored neighbours (>= 0 entries); overflowing shells go to the slow list.
-__global__ void k1_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
-                               const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
-                               const uint8_t* __restrict__ flg, int64_t n, int S, u64 tp, int ti,
-                               uint8_t* inP, int* cand, int* ncand, int* slow, int* nslow) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n || !alive[s]) return;
-    u64 ps = prim[s];
-    int is = pos[s].w;
-    if (key_gt(tp, ti, ps, is)) return;  // below tau
-    if (flg[s] & 2) {
-        slow[atomicAdd(nslow, 1)] = (int)s;
-        return;
-    }
-    bool ok = nbr[s * S] < 0;  // no neighbour at all
-    for (int i = 0; i < S && !ok; i++) {
-        int x = nbr[s * S + i];
-        if (x < 0) continue;
-        if (key_gt(ps, is, prim[x], pos[x].w)) ok = true;
-    }
-    if (ok) {
-        inP[s] = 1;
-        cand[atomicAdd(ncand, 1)] = (int)s;
-    }
-}
-
-// Slow path for overflowing shells: accept iff every live point at distance
-// d1 has a smaller key (then p has no dependency either).
-__global__ void k1_slow_kernel(GridView g, const u64* __restrict__ prim,
-                               const uint8_t* __restrict__ alive, const u64* __restrict__ rk2,
-                               const int* __restrict__ slow, const int* __restrict__ nslow,
-                               uint8_t* inP, int* cand, int* ncand) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nslow) return;
-    int s = slow[t];
-    int4 qp = g.pos[s];
-    u64 r2 = rk2[s];
-    u64 ps = prim[s];
-    int ux = qp.x - g.origin.x, uy = qp.y - g.origin.y, uz = qp.z - g.origin.z;
-    u64 c0 = g.code[s];
-    bool ok = true;
-    for (int L = g.leaf[s]; L <= g.B && ok; L++) {
-        int cx = 0, cy = 0, cz = 0;
-        if (L < g.B) {
-            cx = (int)compact3(c0 >> (3 * L));
-            cy = (int)compact3(c0 >> (3 * L + 1));
-            cz = (int)compact3(c0 >> (3 * L + 2));
-        }
-        // all shell points lie within the cube once r2 < gap^2
-        int sh = L + g.shift;
-        long long q[3] = {ux, uy, uz};
-        int c[3] = {cx, cy, cz};
-        int m[3] = {g.umax.x, g.umax.y, g.umax.z};
-        long long best = -1;
-        for (int a = 0; a < 3; a++) {
-            long long lo = (long long)(c[a] - 1) << sh, hi = (long long)(c[a] + 2) << sh;
-            if (lo > 0 && (best < 0 || q[a] - lo + 1 < best)) best = q[a] - lo + 1;
-            if (hi <= m[a] && (best < 0 || hi - q[a] < best)) best = hi - q[a];
-        }
-        bool covered = L >= g.B || best < 0 || r2 < (u64)best * (u64)best;
-        if (!covered) continue;
-        for (int o = 0; o < 27 && ok; o++) {
-            int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-            uint32_t b, e;
-            int lvl;
-            int rt = resolve_cell(g, L, cx + dx, cy + dy, cz + dz, b, e, &lvl);
-            if (!rt) continue;
-            for (uint32_t j = b; j < e && ok; j++) {
-                if ((int)j == s || !alive[j]) continue;
-                int4 v = g.pos[j];
-                long long dx2 = v.x - qp.x, dy2 = v.y - qp.y, dz2 = v.z - qp.z;
-                u64 d2 = (u64)(dx2 * dx2 + dy2 * dy2 + dz2 * dz2);
-                if (d2 == r2 && key_gt(prim[j], v.w, ps, qp.w)) ok = false;
-            }
-        }
-        // a coarse leaf may be reached twice: harmless for this test
-        if (ok) {
-            inP[s] = 1;
-            cand[atomicAdd(ncand, 1)] = s;
-        }
-        return;
-    }
-}
-
 // (B) for k = 1: a shell member of larger input index must be in P.
 __global__ void k1_fix_kernel(const int* __restrict__ cand, const int* __restrict__ ncand,
                               const int4* __restrict__ pos, const int* __restrict__ nbr, int S,
@@ -237,59 +151,6 @@ __global__ void k1_fix_kernel(const int* __restrict__ cand, const int* __restric
             *changed = 1;
             return;
         }
-    }
-}
-
-// ------------------------------------------------------------------ k >= 2 rule
-// Candidates: key >= tau.  (A) is immediate when every stored neighbour has
-// a smaller key and no further point ties the k-th distance; otherwise the
-// candidate goes to the filtered-search list.  Danger sources: points x with
-// key > tau whose k-ball holds a point of key >= tau (else the k low points
-// of x's ball already shield every candidate).
-__global__ void kk_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
-                               const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
-                               const uint8_t* __restrict__ flg, int64_t n, int S, int k, u64 tp,
-                               int ti, uint8_t* inP, int* cand, int* ncand, uint8_t* fq_flag,
-                               uint8_t* dg_flag) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    fq_flag[s] = 0;
-    dg_flag[s] = 0;
-    if (!alive[s]) return;
-    u64 ps = prim[s];
-    int is = pos[s].w;
-    if (key_gt(tp, ti, ps, is)) return;  // below tau
-    bool lower = !(flg[s] & 1);
-    // a tie at the k-th distance, fewer than k neighbours, or a neighbour of
-    // key >= tau makes s a danger source
-    bool band_nbr = (flg[s] & 1) != 0 || nbr[s * S + k - 1] < 0;
-    for (int i = 0; i < k; i++) {
-        int x = nbr[s * S + i];
-        if (x < 0) continue;
-        u64 px = prim[x];
-        int ix = pos[x].w;
-        if (key_gt(px, ix, ps, is)) lower = false;
-        if (!key_gt(tp, ti, px, ix)) band_nbr = true;
-    }
-    if (lower) {
-        inP[s] = 1;
-        cand[atomicAdd(ncand, 1)] = (int)s;
-    } else {
-        fq_flag[s] = 1;
-    }
-    bool above_tau = key_gt(ps, is, tp, ti);
-    if (above_tau && band_nbr) dg_flag[s] = 1;
-}
-
-__global__ void kk_accept_kernel(const int* __restrict__ list, const int* __restrict__ nlist,
-                                 const u64* __restrict__ prim, const u64* __restrict__ fprim,
-                                 uint8_t* inP, int* cand, int* ncand) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nlist) return;
-    int s = list[t];
-    if (fprim[s] == prim[s]) {
-        inP[s] = 1;
-        cand[atomicAdd(ncand, 1)] = s;
     }
 }
 
@@ -620,22 +481,6 @@ __global__ void remove_kernel(const int* __restrict__ cand, const int* __restric
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(removed, (unsigned long long)c);
 }
 
-// A live point must be searched again when one of its first `kchk` stored
-// neighbours was removed (its k-nearest distance list changed).
-__global__ void dirty_kernel(const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
-                             int64_t n, int S, int kchk, uint8_t* dirty) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    uint8_t d = 0;
-    if (alive[s]) {
-        for (int i = 0; i < kchk; i++) {
-            int x = nbr[s * S + i];
-            if (x >= 0 && !alive[x]) d = 1;
-        }
-    }
-    dirty[s] = d;
-}
-
 __global__ void keep_kernel(const int4* __restrict__ pos, const uint8_t* __restrict__ alive,
                             int64_t n, uint8_t* keep) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -728,51 +573,11 @@ cudaError_t launch_sel_compact(const u64* prim, const int4* pos, const uint8_t* 
                                                oi, ocount); note_launch();
     return cudaGetLastError();
 }
-cudaError_t launch_k1_cand(const u64* prim, const int4* pos, const uint8_t* alive, const int* nbr,
-                           const uint8_t* flg, int64_t n, int S, u64 tp, int ti, uint8_t* inP,
-                           int* cand, int* ncand, int* slow, int* nslow, cudaStream_t st) {
-    k1_cand_kernel<<<GRID1(n), 0, st>>>(prim, pos, alive, nbr, flg, n, S, tp, ti, inP, cand, ncand,
-                                        slow, nslow); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t launch_k1_slow(const GridView& g, const u64* prim, const uint8_t* alive,
-                           const u64* rk2, const int* slow, const int* nslow, int max_slow,
-                           uint8_t* inP, int* cand, int* ncand, cudaStream_t st) {
-    if (max_slow <= 0) return cudaSuccess;
-    k1_slow_kernel<<<GRID1(max_slow), 0, st>>>(g, prim, alive, rk2, slow, nslow, inP, cand, ncand); note_launch();
-    return cudaGetLastError();
-}
 cudaError_t launch_k1_fix(const int* cand, const int* ncand, int max_cand, const int4* pos,
                           const int* nbr, int S, const uint8_t* inP, uint8_t* rej, int* changed,
                           cudaStream_t st) {
     if (max_cand <= 0) return cudaSuccess;
     k1_fix_kernel<<<GRID1(max_cand), 0, st>>>(cand, ncand, pos, nbr, S, inP, rej, changed); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t launch_kk_cand(const u64* prim, const int4* pos, const uint8_t* alive, const int* nbr,
-                           const uint8_t* flg, int64_t n, int S, int k, u64 tp, int ti,
-                           uint8_t* inP, int* cand, int* ncand, uint8_t* fq_flag,
-                           uint8_t* dg_flag, cudaStream_t st) {
-    kk_cand_kernel<<<GRID1(n), 0, st>>>(prim, pos, alive, nbr, flg, n, S, k, tp, ti, inP, cand,
-                                        ncand, fq_flag, dg_flag); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t launch_kk_accept(const int* list, const int* nlist, int max_list, const u64* prim,
-                             const u64* fprim, uint8_t* inP, int* cand, int* ncand,
-                             cudaStream_t st) {
-    if (max_list <= 0) return cudaSuccess;
-    kk_accept_kernel<<<GRID1(max_list), 0, st>>>(list, nlist, prim, fprim, inP, cand, ncand); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t launch_danger(const GridView& g, const int* src, const int* nsrc, int max_src,
-                          const u64* prim, const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
-                          const u64* lam, int k, int2* pairs, int* npairs, int pair_cap,
-                          int* overflow, unsigned long long* diag, cudaStream_t st) {
-    if (max_src <= 0) return cudaSuccess;
-    unsigned blocks = (unsigned)((max_src + DG_WARPS - 1) / DG_WARPS);
-    danger_kernel<<<blocks, DG_WARPS * 32, 0, st>>>(g, src, nsrc, prim, alive, inP, rej, lam,
-                                                    nullptr, 0, k, pairs, npairs, pair_cap,
-                                                    overflow, diag, nullptr, nullptr); note_launch();
     return cudaGetLastError();
 }
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
@@ -803,11 +608,6 @@ cudaError_t launch_remove(const int* cand, const int* ncand, int max_cand, uint8
     cudaError_t e = cudaMemsetAsync(removed, 0, sizeof(unsigned long long), st);
     if (e || max_cand <= 0) return e;
     remove_kernel<<<GRID1(max_cand), 0, st>>>(cand, ncand, inP, rej, alive, removed); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t launch_dirty(const uint8_t* alive, const int* nbr, int64_t n, int S, int kchk,
-                         uint8_t* dirty, cudaStream_t st) {
-    dirty_kernel<<<GRID1(n), 0, st>>>(alive, nbr, n, S, kchk, dirty); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_keep(const int4* pos, const uint8_t* alive, int64_t n, uint8_t* keep,

@@ -296,51 +296,6 @@ __global__ void k1d_fix_kernel(const int* __restrict__ cand, const int4* __restr
     }
 }
 
-// ------------------------------------------------------------------ k >= 2
-__global__ void kkd_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
-                                const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
-                                const uint8_t* __restrict__ flg, int64_t n, int S, int k,
-                                RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
-                                uint8_t* dg_flag, int* src) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool fq = false;
-    if (s < n) {
-        uint8_t dgv = 0;
-        if (alive[s]) {
-            u64 tp = rd->tau_prim;
-            int ti = rd->tau_idx;
-            u64 ps = prim[s];
-            int is = pos[s].w;
-            if (!key_gt(tp, ti, ps, is)) {
-                bool lower = !(flg[s] & 1);
-                bool band_nbr = (flg[s] & 1) != 0 || nbr[s * S + k - 1] < 0;
-                for (int i = 0; i < k; i++) {
-                    int x = nbr[s * S + i];
-                    if (x < 0) continue;
-                    u64 px = prim[x];
-                    int ix = pos[x].w;
-                    if (key_gt(px, ix, ps, is)) lower = false;
-                    if (!key_gt(tp, ti, px, ix)) band_nbr = true;
-                }
-                if (lower) {
-                    inP[s] = 1;
-                    cand[atomicAdd(&rd->ncand, 1)] = (int)s;
-                } else {
-                    fq = true;
-                }
-                if (key_gt(ps, is, tp, ti) && band_nbr) {
-                    dgv = 1;
-                    src[atomicAdd(&rd->nsrc, 1)] = (int)s;
-                }
-            }
-        }
-        fq_flag[s] = fq ? 1 : 0;
-        dg_flag[s] = dgv;
-    }
-    unsigned c = __popc(__ballot_sync(FULLM, fq));
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->tot_filtered, (unsigned long long)c);
-}
-
 __global__ void kkd_accept_kernel(const uint8_t* __restrict__ fq_flag, const u64* __restrict__ prim,
                                   const u64* __restrict__ fprim, int64_t n, RoundDev* rd,
                                   uint8_t* inP, int* cand) {
@@ -604,15 +559,6 @@ cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* a
     for (int it = 0; it < PD_FIX_ITERS; it++) {
         k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, g.pos, nbr, S, inP, rej, it, rd); note_launch();
     }
-    return cudaGetLastError();
-}
-
-cudaError_t round_launch_kk_cand(const u64* prim, const int4* pos, const uint8_t* alive,
-                                 const int* nbr, const uint8_t* flg, int64_t n, int S, int k,
-                                 RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
-                                 uint8_t* dg_flag, int* src, cudaStream_t st) {
-    kkd_cand_kernel<<<GRID1(n), 0, st>>>(prim, pos, alive, nbr, flg, n, S, k, rd, inP, cand,
-                                         fq_flag, dg_flag, src); note_launch();
     return cudaGetLastError();
 }
 
