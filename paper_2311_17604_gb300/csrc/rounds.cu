@@ -161,6 +161,7 @@ __global__ void k1_fix_kernel(const int* __restrict__ cand, const int* __restric
 // could enter x's k nearest before it is popped: record (x, p).
 #define DG_CAP 512
 #define DG_WARPS 2
+#define DG_BLOCKS_PER_SM 14  // resident blocks per SM (registers capped to fit)
 #define PD_DG_SMAX 8  // stored neighbours used as shields (S up to 8)
 
 __device__ inline u64 box_d2x(int ux, int uy, int uz, int bx, int by, int bz, int sh) {
@@ -378,15 +379,14 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
                 bool near = false;
                 u64 d2 = 0, ky = 0;
                 int oy = 0;
-                if (j < e && (int)j != x && alive[j]) {
+                if (j < e) {  // independent loads, issued together
+                    uint8_t al = alive[j];
                     int4 v = g.pos[j];
+                    ky = prim[j];
                     long long ddx = v.x - xp.x, ddy = v.y - xp.y, ddz = v.z - xp.z;
                     d2 = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
-                    near = d2 <= dmax;
-                    if (near) {
-                        ky = prim[j];
-                        oy = v.w;
-                    }
+                    near = al && (int)j != x && d2 <= dmax;
+                    oy = v.w;
                 }
                 unsigned nb = __ballot_sync(FULLM, near);
                 if (near) {
@@ -421,7 +421,7 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
     }
 }
 
-__global__ void __launch_bounds__(DG_WARPS * 32)
+__global__ void __launch_bounds__(DG_WARPS * 32, DG_BLOCKS_PER_SM)
     danger_kernel(GridView g, const int* __restrict__ src, const int* __restrict__ nsrc,
                   const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
                   const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
@@ -584,7 +584,7 @@ cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* pr
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
                                 int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
-    danger_kernel<<<152 * 10, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
+    danger_kernel<<<152 * DG_BLOCKS_PER_SM, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
                                                      &rd->cap_over, csorted, &rd->ncs); note_launch();
