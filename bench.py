@@ -51,6 +51,11 @@ WORKLOADS = {
                          "ground + 40 boxes + 20 spheres at 1-60 m, int32 mm; k=4; keep 10%",
                     gen=lambda seed: synth.outdoor_scan(seed=seed, n_az=10000, n_el=2000),
                     k=4, ratio=0.1, sample=400_000, ref_sample=150_000),
+    "site": dict(desc="merged site scan, 4 stations x 10000x2500 rays (100M points) of the "
+                      "200x200x30 m site generator (the 1B-point 40-station configuration "
+                      "scaled to 4 stations), int32 mm; k=1; keep 5%",
+                 gen=lambda seed: synth.site_scan(seed=seed, station_ids=[0, 1, 2, 3], rgb=False),
+                 k=1, ratio=0.05, sample=400_000, ref_sample=150_000),
     "room": dict(desc="room single-station scan, 1000x200 rays, 10x8x3 m, 3 boxes, "
                       "2 mm noise, int32 mm; k=1; keep 25%",
                  gen=lambda seed: synth.room_scan(seed=seed, n_az=1000, n_el=200),
