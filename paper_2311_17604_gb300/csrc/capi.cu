@@ -112,6 +112,7 @@ struct pd_grid {
     u64* hz;  // k+b buffer horizon
     int* glist;  // flagged searches: groups holding a flagged query, and their count
     int* gcount;
+    u64* cmin;   // during a decimation: least live key of every 32-position chunk
     // small device scalars
     int* d_int;                  // [0] ngroups, [1..7] counters
     unsigned long long* d_u64;   // [0] counts
@@ -256,7 +257,7 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
                     g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64, g->glist,
-                    g->gcount};
+                    g->gcount, g->cmin};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -414,6 +415,7 @@ KnnArgs base_args(pd_grid* g, const pd_cost_params* cp) {
     a.rk2_out = g->rk2;
     a.flg_out = g->flg;
     a.hz_out = g->hz;
+    a.cmin = g->cmin;
     return a;
 }
 
@@ -823,6 +825,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         ALLOC(lam, u64, cap);
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
         ALLOC(pairs, int2, pair_cap);
+        ALLOC(g->cmin, u64, (cap + 31) / 32 + 1);
     }
     SelBuffers sb;
     ALLOC(sb.p[0], u64, cap);
@@ -867,6 +870,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             BufView bv = bufview(g, cp);
             CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,
                                      g->st));
+            CK(launch_chunk_min(g->prim, g->alive, g->ng, g->cmin, g->st));
             {
                 Span t(T, &g->stats.ms_knn);
                 rc = knn_flag(g, cp, FILT_BELOW_SELF, Sf, fqf, fprim, rd);
@@ -948,6 +952,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.danger_queries = (int64_t)h.tot_lambda;
     CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
     CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
+    gfree(g, g->cmin);
+    g->cmin = nullptr;
     void* fr[] = {inP, rej, dirty, cand, slow, src, csort, fqf, dgf, fprim, lam, pairs,
                   sb.p[0], sb.p[1], sb.i[0], sb.i[1], sb.hist, rd};
     for (void* p : fr) gfree(g, p);

@@ -318,9 +318,15 @@ __device__ inline double cost_sum(const KnnArgs& a, int q, const TL& top, int k)
 template <int S, int FILT, bool W, class TL, typename D>
 __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, uint32_t b,
                                            uint32_t e, int q, int4 qp, bool todo, u64 tp, int ti,
-                                           TL& top, int4* sp, u64* sk, int* so, int lane, int sub,
-                                           int lpq) {
+                                           u64 tpmax, TL& top, int4* sp, u64* sk, int* so,
+                                           int lane, int sub, int lpq) {
     for (uint32_t c = b; c < e; c += 32) {
+        if (FILT != FILT_NONE && a.cmin) {
+            // no key of these 32 positions is below any lane's threshold: skip
+            uint32_t last = min(c + 31u, e - 1u);
+            u64 m0 = a.cmin[c >> 5], m1 = a.cmin[last >> 5];
+            if ((m0 < m1 ? m0 : m1) > tpmax) continue;
+        }
         uint32_t j = c + lane;
         int4 v = make_int4(0, 0, 0, -1);
         if (j < e) {
@@ -406,7 +412,8 @@ __device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& 
 template <int S, int FILT, bool W, class TL, bool PACK>
 __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, int L, int R,
                                           int q, int4 qp, int ux, int uy, int uz, bool& todo,
-                                          u64 tp, int ti, int lane, int sub, int lpq, int rt,
+                                          u64 tp, int ti, u64 tpmax, int lane, int sub, int lpq,
+                                          int rt,
                                           uint32_t rb, uint32_t re, int rl, int bx, int by,
                                           int bz, int cx, int cy, int cz, int4* sp, u64* sk,
                                           int* so, unsigned long long& wpairs) {
@@ -430,11 +437,11 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
             wpairs += (unsigned long long)(e - b) * (unsigned long long)nqt;
         }
         if (PACK || lv + g.shift <= 13)
-            scan_range<S, FILT, W, TL, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, top, sp, sk, so,
-                                                 lane, sub, lpq);
+            scan_range<S, FILT, W, TL, uint32_t>(g, a, b, e, q, qp, todo, tp, ti, tpmax, top, sp,
+                                                 sk, so, lane, sub, lpq);
         else
-            scan_range<S, FILT, W, TL, u64>(g, a, b, e, q, qp, todo, tp, ti, top, sp, sk, so, lane,
-                                            sub, lpq);
+            scan_range<S, FILT, W, TL, u64>(g, a, b, e, q, qp, todo, tp, ti, tpmax, top, sp, sk, so,
+                                            lane, sub, lpq);
     }
     // merge the partial lists of each query's lanes (butterfly)
     for (int off = lpq >> 1; off >= 1; off >>= 1) top.merge_xor(off, todo);
@@ -487,6 +494,14 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
         tp = a.rd ? a.rd->tau_prim : a.tau_prim;
         ti = a.rd ? a.rd->tau_idx : a.tau_idx;
     }
+    // the largest threshold of the warp's queries (chunk skipping)
+    u64 tpmax = q >= 0 ? tp : 0;
+    if (FILT == FILT_BELOW_SELF) {
+        for (int off = 16; off; off >>= 1) {
+            u64 o = __shfl_xor_sync(FULLM, tpmax, off);
+            tpmax = o > tpmax ? o : tpmax;
+        }
+    }
     // exactness bound: the R-th smallest distance must be exact
     // k = 1 density: the nearest distance and its complete shell; other full
     // searches: all S stored neighbours exact (the k+b neighbour buffer, so a
@@ -533,11 +548,11 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
         bool pack = __all_sync(FULLM, !rt || rl + g.shift <= 13);
         if (pack)
             knn_level<S, FILT, W, TopPack<S, W>, true>(g, a, L, R, q, qp, ux, uy, uz, todo, tp, ti,
-                                                       lane, sub, lpq, rt, rb, re, rl, bx, by, bz,
+                                                       tpmax, lane, sub, lpq, rt, rb, re, rl, bx, by, bz,
                                                        cx, cy, cz, sp, sk, so, wpairs);
         else
             knn_level<S, FILT, W, TopList<S, W>, false>(g, a, L, R, q, qp, ux, uy, uz, todo, tp,
-                                                        ti, lane, sub, lpq, rt, rb, re, rl, bx, by,
+                                                        ti, tpmax, lane, sub, lpq, rt, rb, re, rl, bx, by,
                                                         bz, cx, cy, cz, sp, sk, so, wpairs);
         L++;
     }
@@ -558,6 +573,22 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
         int gid = blockIdx.x * PD_WARPS + w;
         if (gid < a.ngroups) knn_group<S, FILT, W>(g, a, gid, s_p[w], s_k[w], s_o[w], lane);
     }
+}
+
+// One warp per aligned chunk of 32 Morton positions: the least live key primary.
+__global__ void chunk_min_kernel(const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
+                                 int64_t n, u64* cmin) {
+    int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t nc = (n + 31) >> 5;
+    if (c >= nc) return;  // whole warps leave together
+    int64_t j = c * 32 + lane;
+    u64 v = (j < n && alive[j]) ? prim[j] : ~0ull;
+    for (int off = 16; off; off >>= 1) {
+        u64 o = __shfl_xor_sync(FULLM, v, off);
+        v = o < v ? o : v;
+    }
+    if (lane == 0) cmin[c] = v;
 }
 
 // Append every group holding a flagged query to glist (one atomic per warp).
@@ -608,6 +639,15 @@ static cudaError_t launch_knn_s(const GridView& g, const KnnArgs& a, cudaStream_
         case FILT_BELOW_SELF: return launch_knn_t<S, FILT_BELOW_SELF>(g, a, st);
         default: return launch_knn_t<S, FILT_BELOW_TAU>(g, a, st);
     }
+}
+
+cudaError_t launch_chunk_min(const u64* prim, const uint8_t* alive, int64_t n, u64* cmin,
+                             cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t threads = ((n + 31) >> 5) * 32;
+    chunk_min_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(prim, alive, n, cmin);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, int* gcount,

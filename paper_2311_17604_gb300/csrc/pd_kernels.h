@@ -105,12 +105,18 @@ struct KnnArgs {
     u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
     u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
     unsigned long long* pairs_out;  // optional: + (query, candidate) pairs scanned
+    const u64* cmin;          // filtered searches: least live key primary of every aligned
+                              //   32-position chunk (chunks above the threshold are skipped)
     const int* glist;         // group-list mode: process groups glist[0 .. *gcount)
     const int* gcount;        //   (device count; a persistent grid walks the list)
 };
 // Flagged mode without a host read: list the groups that hold a flagged query
 // (a.qflag), then run the search over that list only.  glist: ngroups ints,
 // gcount: one int, both device scratch.
+// cmin[c] = least key primary of the live points at Morton positions
+// [32c, 32c + 32) (~0 when none), for the chunk skipping of filtered searches.
+cudaError_t launch_chunk_min(const u64* prim, const uint8_t* alive, int64_t n, u64* cmin,
+                             cudaStream_t st);
 cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, int* gcount,
                                cudaStream_t st);
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
