@@ -323,6 +323,7 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
     for (uint32_t c = b; c < e; c += 32) {
         if (FILT != FILT_NONE && a.cmin) {
             // no key of these 32 positions is below any lane's threshold: skip
+            // (c, e and tpmax are warp-uniform, so the whole warp skips)
             uint32_t last = min(c + 31u, e - 1u);
             u64 m0 = a.cmin[c >> 5], m1 = a.cmin[last >> 5];
             if ((m0 < m1 ? m0 : m1) > tpmax) continue;
@@ -494,9 +495,11 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
         tp = a.rd ? a.rd->tau_prim : a.tau_prim;
         ti = a.rd ? a.rd->tau_idx : a.tau_idx;
     }
-    // the largest threshold of the warp's queries (chunk skipping)
+    // the largest threshold of the warp's queries (chunk skipping); reduced
+    // over all 32 lanes so that every lane holds the same value: the skip in
+    // scan_range must be taken by the whole warp or by none of it
     u64 tpmax = q >= 0 ? tp : 0;
-    if (FILT == FILT_BELOW_SELF) {
+    if (FILT != FILT_NONE) {
         for (int off = 16; off; off >>= 1) {
             u64 o = __shfl_xor_sync(FULLM, tpmax, off);
             tpmax = o > tpmax ? o : tpmax;
