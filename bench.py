@@ -186,8 +186,8 @@ def run_reference(args, wl, rank):
 # DRAM bytes per query of knn_kernel<8,0> (the first full pass), from one
 # `ncu --set full` capture of `bench.py --knn-only` on the outdoor scan, valid
 # while the kernel's sources hash to KNN_SRC_SHA (else traffic is reported null).
-KNN_SRC_SHA = "8248d19240611468"
-KNN_DRAM_BYTES_PER_QUERY = 111.8   # 526.5 MB read + 634.3 MB written / 10,385,229 queries
+KNN_SRC_SHA = "1d194461d3f93c2c"
+KNN_DRAM_BYTES_PER_QUERY = 111.7   # 525.3 MB read + 634.4 MB written / 10,385,229 queries
 KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
                "paper_2311_17604_gb300/csrc/pd_kernels.h"]
 ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop: exact int distance test
