@@ -805,7 +805,6 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     bool use_buf = !g->density_k1 && S <= 8;
     uint8_t *inP, *rej, *dirty, *fqf = nullptr, *dgf = nullptr;  // dgf: lambda search flags
     int *cand, *slow, *src = nullptr, *csort = nullptr;
-    uint32_t* cpre = nullptr;
     u64 *fprim = nullptr, *lam = nullptr;
     int2* pairs = nullptr;
     int64_t cap = g->n;
@@ -827,7 +826,6 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
         ALLOC(pairs, int2, pair_cap);
         ALLOC(g->cmin, u64, (cap + 31) / 32 + 1);
-        ALLOC(cpre, uint32_t, cap + 1);
     }
     SelBuffers sb;
     ALLOC(sb.p[0], u64, cap);
@@ -886,12 +884,10 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             }
             {
                 Span t(T, &g->stats.ms_danger);
-                // candidates in Morton order, and their prefix counts over Morton
-                // positions, so each source finds its own in two loads per cell
+                // candidates in Morton order, so each source finds its own by search
                 CK(stable_compact(inP, g->ng, csort, &rd->ncs, scratch_of(g), g->st));
-                CK(launch_prefix_count(inP, g->ng, cpre, scratch_of(g), g->st));
                 CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k,
-                                       pairs, pair_cap, csort, cpre, rd, g->st));
+                                       pairs, pair_cap, csort, rd, g->st));
             }
             CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
         }
@@ -958,7 +954,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
     gfree(g, g->cmin);
     g->cmin = nullptr;
-    void* fr[] = {inP, rej, dirty, cand, slow, src, csort, cpre, fqf, dgf, fprim, lam, pairs,
+    void* fr[] = {inP, rej, dirty, cand, slow, src, csort, fqf, dgf, fprim, lam, pairs,
                   sb.p[0], sb.p[1], sb.i[0], sb.i[1], sb.hist, rd};
     for (void* p : fr) gfree(g, p);
     cudaEventRecord(e1, g->st);

@@ -148,11 +148,7 @@ cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, cons
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
-                                int pair_cap, const int* csorted, const uint32_t* cpre,
-                                RoundDev* rd, cudaStream_t st);
-// out[j] = number of nonzero flag[i] with i < j, for j in [0, n] (exclusive prefix count)
-cudaError_t launch_prefix_count(const uint8_t* flag, int64_t n, uint32_t* out, const Scratch& s,
-                                cudaStream_t st);
+                                int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_pairs_fix(const int2* pairs, int pair_cap, const uint8_t* inP,
                                    uint8_t* rej, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_remove(const int* cand, uint8_t* inP, uint8_t* rej, uint8_t* alive,

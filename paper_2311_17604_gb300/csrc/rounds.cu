@@ -224,7 +224,6 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
                            uint8_t* rej, const u64* __restrict__ lam, const int* __restrict__ nbr,
                            int S, int k, int2* pairs, int* npairs, int pair_cap, int* overflow,
                            unsigned long long* diag, const int* __restrict__ csorted,
-                           const uint32_t* __restrict__ cpre,
                            const int* __restrict__ ncs, DangerSmem& sm, int w, int lane) {
     int(&c_j)[DG_WARPS][DG_CAP] = sm.c_j;
     u64(&c_d)[DG_WARPS][DG_CAP] = sm.c_d;
@@ -267,12 +266,7 @@ __device__ void danger_one(const GridView& g, int x, const u64* __restrict__ pri
     // range's points are streamed and filtered
     int nc = 0;
     uint32_t cs_lo = 0, cs_hi = 0;
-    if (cpre && rt) {
-        // prefix counts of the candidate flags over Morton positions: the
-        // slice of the sorted list that falls in [rb, re) in two loads
-        cs_lo = cpre[rb];
-        cs_hi = cpre[re];
-    } else if (csorted && rt) {
+    if (csorted && rt) {
         int nlist = *ncs;
         int lo = 0, hi = nlist;
         while (lo < hi) {
@@ -433,14 +427,13 @@ __global__ void __launch_bounds__(DG_WARPS * 32, DG_BLOCKS_PER_SM)
                   const uint8_t* __restrict__ inP, uint8_t* rej, const u64* __restrict__ lam,
                   const int* __restrict__ nbr, int S, int k, int2* pairs, int* npairs,
                   int pair_cap, int* overflow, unsigned long long* diag,
-                  const int* __restrict__ csorted, const int* __restrict__ ncs,
-                  const uint32_t* __restrict__ cpre) {
+                  const int* __restrict__ csorted, const int* __restrict__ ncs) {
     __shared__ DangerSmem sm;
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int ns = *nsrc;
     for (int t = blockIdx.x * DG_WARPS + w; t < ns; t += gridDim.x * DG_WARPS)
         danger_one(g, src[t], prim, alive, inP, rej, lam, nbr, S, k, pairs, npairs, pair_cap,
-                   overflow, diag, csorted, cpre, ncs, sm, w, lane);
+                   overflow, diag, csorted, ncs, sm, w, lane);
 }
 
 // Fallback: accept every live point with key >= tau (tau = the top key).
@@ -590,29 +583,13 @@ cudaError_t launch_k1_fix(const int* cand, const int* ncand, int max_cand, const
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
-                                int pair_cap, const int* csorted, const uint32_t* cpre,
-                                RoundDev* rd, cudaStream_t st) {
+                                int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
     danger_kernel<<<152 * DG_BLOCKS_PER_SM, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
-                                                     &rd->cap_over, csorted, &rd->ncs, cpre); note_launch();
+                                                     &rd->cap_over, csorted, &rd->ncs); note_launch();
     return cudaGetLastError();
 }
-__global__ void flag_u32_kernel(const uint8_t* __restrict__ f, int64_t n, uint32_t* out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = f[i] != 0;
-    else if (i == n) out[n] = 0;
-}
-
-cudaError_t launch_prefix_count(const uint8_t* flag, int64_t n, uint32_t* out, const Scratch& s,
-                                cudaStream_t st) {
-    flag_u32_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, st>>>(flag, n, out);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e) return e;
-    return exclusive_scan_u32(out, n + 1, s, st);
-}
-
 cudaError_t launch_accept_above(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
                                 u64 tp, int ti, uint8_t* inP, int* cand, int* ncand,
                                 cudaStream_t st) {
