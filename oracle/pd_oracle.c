@@ -23,6 +23,10 @@
  *     and the colour-deviation term, for which the paper prints no formula):
  *         orientation  w = 1 - a * (1 - |n_p . n_q|)
  *         colour       w = 1 - a * ||rgb_p - rgb_q||_2 / (255 * sqrt(3))
+ *     Parity unpinned: these two weights are readings of the paper (it gives
+ *     no colour formula, and the orientation term is read with |n_p . n_q|
+ *     for unoriented normals), so no printed value or closed form checks
+ *     them; the tests check them only against the same formula recomputed.
  *   - Greedy removal (section "Computing per-sample costs", after Eq. 7, and
  *     section "Sub-sampling algorithm", step 2): repeatedly remove the live
  *     point with the largest key (cost, index) -- among equal costs the larger
