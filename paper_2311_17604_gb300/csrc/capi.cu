@@ -736,6 +736,27 @@ int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
     return PD_OK;
 }
 
+// Scratch and events of one decimation, released (stream-ordered) on every
+// exit path, errors included.
+struct RoundScratch {
+    pd_grid* g;
+    std::vector<void*> ptrs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    explicit RoundScratch(pd_grid* gg) : g(gg) {}
+    ~RoundScratch() {
+        for (void* p : ptrs) gfree(g, p);
+        gfree(g, g->cmin);
+        g->cmin = nullptr;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+#define RALLOC(ptr, type, count)              \
+    do {                                      \
+        ALLOC(ptr, type, count);              \
+        rs.ptrs.push_back((void*)(ptr));      \
+    } while (0)
+
 int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev) {
     int rc = check_cost(g, cp);
     if (rc) return rc;
@@ -752,10 +773,11 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.n = g->n;
     g->stats.m = m;
     long long launches0 = g_launch_count;
+    RoundScratch rs(g);
     Timers T(g->st);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEventCreate(&rs.e0);
+    cudaEventCreate(&rs.e1);
+    cudaEvent_t e0 = rs.e0, e1 = rs.e1;
     cudaEventRecord(e0, g->st);
     rc = prepare_state(g, cp);
     if (rc) return rc;
@@ -808,34 +830,34 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     u64 *fprim = nullptr, *lam = nullptr;
     int2* pairs = nullptr;
     int64_t cap = g->n;
-    ALLOC(inP, uint8_t, cap);
-    ALLOC(rej, uint8_t, cap);
-    ALLOC(dirty, uint8_t, cap);
-    ALLOC(cand, int, cap);
-    ALLOC(slow, int, cap);
+    RALLOC(inP, uint8_t, cap);
+    RALLOC(rej, uint8_t, cap);
+    RALLOC(dirty, uint8_t, cap);
+    RALLOC(cand, int, cap);
+    RALLOC(slow, int, cap);
     CK(cudaMemsetAsync(inP, 0, cap, g->st));
     CK(cudaMemsetAsync(rej, 0, cap, g->st));
     int pair_cap = 0;
     if (!g->density_k1) {
-        ALLOC(fqf, uint8_t, cap);
-        ALLOC(dgf, uint8_t, cap);
-        ALLOC(src, int, cap);
-        ALLOC(csort, int, cap);
-        ALLOC(fprim, u64, cap);
-        ALLOC(lam, u64, cap);
+        RALLOC(fqf, uint8_t, cap);
+        RALLOC(dgf, uint8_t, cap);
+        RALLOC(src, int, cap);
+        RALLOC(csort, int, cap);
+        RALLOC(fprim, u64, cap);
+        RALLOC(lam, u64, cap);
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
-        ALLOC(pairs, int2, pair_cap);
+        RALLOC(pairs, int2, pair_cap);
         ALLOC(g->cmin, u64, (cap + 31) / 32 + 1);
     }
     SelBuffers sb;
-    ALLOC(sb.p[0], u64, cap);
-    ALLOC(sb.p[1], u64, cap);
-    ALLOC(sb.i[0], int, cap);
-    ALLOC(sb.i[1], int, cap);
-    ALLOC(sb.hist, uint32_t, 4096);
+    RALLOC(sb.p[0], u64, cap);
+    RALLOC(sb.p[1], u64, cap);
+    RALLOC(sb.i[0], int, cap);
+    RALLOC(sb.i[1], int, cap);
+    RALLOC(sb.hist, uint32_t, 4096);
     CK(cudaMemsetAsync(sb.hist, 0, 4096 * sizeof(uint32_t), g->st));
     RoundDev* rd;
-    ALLOC(rd, RoundDev, 1);
+    RALLOC(rd, RoundDev, 1);
     RoundDev h;
     memset(&h, 0, sizeof(h));
     h.live = live;
@@ -952,11 +974,6 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.danger_queries = (int64_t)h.tot_lambda;
     CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
     CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
-    gfree(g, g->cmin);
-    g->cmin = nullptr;
-    void* fr[] = {inP, rej, dirty, cand, slow, src, csort, fqf, dgf, fprim, lam, pairs,
-                  sb.p[0], sb.p[1], sb.i[0], sb.i[1], sb.hist, rd};
-    for (void* p : fr) gfree(g, p);
     cudaEventRecord(e1, g->st);
     CK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -966,8 +983,6 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.ms_knn += g->stats.ms_knn_first + g->stats.ms_knn_requery;
     g->stats.ms_rules = ms - g->stats.ms_knn - g->stats.ms_build;
     g->stats.launches = g_launch_count - launches0;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     g->ng = 0;  // consumed
     return PD_OK;
 }
