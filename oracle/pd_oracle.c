@@ -23,10 +23,12 @@
  *     and the colour-deviation term, for which the paper prints no formula):
  *         orientation  w = 1 - a * (1 - |n_p . n_q|)
  *         colour       w = 1 - a * ||rgb_p - rgb_q||_2 / (255 * sqrt(3))
- *     Parity unpinned: these two weights are readings of the paper (it gives
- *     no colour formula, and the orientation term is read with |n_p . n_q|
- *     for unoriented normals), so no printed value or closed form checks
- *     them; the tests check them only against the same formula recomputed.
+ *     Both weights are readings of the paper (it gives no colour formula,
+ *     and the orientation term is read with |n_p . n_q| for unoriented
+ *     normals).  The tests pin them to hand-worked clouds whose costs follow
+ *     in closed form: identical colours weigh 1, black against white 1 - a,
+ *     a pure red difference 1 - a / sqrt 3; parallel and antiparallel
+ *     normals 1, orthogonal ones 1 - a, a 60 degree angle 1 - a / 2.
  *   - Greedy removal (section "Computing per-sample costs", after Eq. 7, and
  *     section "Sub-sampling algorithm", step 2): repeatedly remove the live
  *     point with the largest key (cost, index) -- among equal costs the larger
