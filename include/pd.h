@@ -224,17 +224,23 @@ int pd_decimate_batch(pd_ctx* ctx, pd_scan_desc* scans, int nscans, const pd_cos
  *             (may be NULL) -- the same layout as pd_knn_cost.
  * All temporaries live in one file-scope device array of
  * PD_STATIC_SCRATCH_BYTES bytes that every GPU loading the library holds until
- * the process exits.  The call makes no cudaMalloc / cudaFree / cudaMallocAsync
- * and uses no allocating library routine.  The first call on a device looks
- * up the array's device address on that device (cudaGetSymbolAddress) and
- * caches it: make that first call before any stream capture.  Every call
- * reuses the same array and overwrites it; it clears what must start at
- * zero.  Two calls that overlap on the GPU (different streams, devices sharing
- * nothing else) race on the array: serialise them.  The call synchronises the
- * stream (it reads the cloud's extent and cell count, like pd_build_grid).
+ * the process exits (each device has its own copy).  The call makes no
+ * cudaMalloc / cudaFree / cudaMallocAsync and uses no allocating library
+ * routine.  The first call on a device looks up the array's device address on
+ * that device (cudaGetSymbolAddress) and caches it for the process: make that
+ * first call before any stream capture.  A cudaDeviceReset (or any teardown of
+ * the device's primary context) invalidates the cached address; do not call
+ * this entry point on that device afterwards.  Every call reuses the same
+ * array and overwrites it; it clears what must start at zero.  Two calls that
+ * overlap on the same device (for example on two streams) race on the array:
+ * serialise them.  Calls on different devices use different copies and do
+ * not race.  The call synchronises the stream (it reads the cloud's extent
+ * and cell count, like pd_build_grid).
  * Returns PD_EINVAL (NULL xyz, n < 1, k outside [1, 16]), PD_ERANGE (n above
- * PD_STATIC_MAX_POINTS, or a coordinate spread >= 2^25 mm), PD_ENOMEM (the
- * cloud needs more octree cells than the fixed table holds), PD_ECUDA.
+ * PD_STATIC_MAX_POINTS, or a coordinate spread >= 2^25 mm), PD_ENOMEM (a
+ * guard: the cloud needs more octree cells than the fixed table holds; with
+ * at most PD_STATIC_MAX_POINTS points and leaves of 32 points the cell count
+ * stays far below the table's size), PD_ECUDA.
  */
 #define PD_STATIC_MAX_POINTS 65536
 #define PD_STATIC_SCRATCH_BYTES (16u << 20)

@@ -41,10 +41,12 @@ def test_static_entry_point_matches_pd_knn_cost_on_consecutive_calls():
     clouds = [synth.room_scan(seed=2, n_az=240, n_el=60).xyz,       # 14,400 points
               synth.random_cloud(3, 5000, 40),                       # duplicates and ties
               synth.random_cloud(4, pd.PD_STATIC_MAX_POINTS, 3000)]  # the largest size
-    for x in clouds:
+    for ci, x in enumerate(clouds):
         n = x.shape[0]
         xd = torch.from_numpy(x).cuda()
-        for k in (1, 4):
+        # k = 16 (17 stored neighbours) is the largest user of the array:
+        # run it at the largest size
+        for k in ((1, 4, 16) if ci == len(clouds) - 1 else (1, 4)):
             g = pd.Grid(ctx, xd)
             cost_ref, knn_ref = pd.pd_knn_cost(g, k=k)
             g.free()
@@ -69,3 +71,14 @@ def test_static_entry_point_rejects_oversized_clouds():
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert L.pd_knn_cost_static(_p(big), n, 1, None, None, stream) == pd.PD_ERANGE
     assert L.pd_knn_cost_static(_p(big), 10, 0, None, None, stream) == pd.PD_EINVAL
+    assert L.pd_knn_cost_static(_p(big), 10, 17, None, None, stream) == pd.PD_EINVAL
+    # a coordinate spread of 2^25 mm: squared distances would leave the exact range
+    wide = torch.tensor([[0, 0, 0], [1 << 25, 0, 0], [5, 5, 5]], dtype=torch.int32,
+                        device="cuda")
+    assert L.pd_knn_cost_static(_p(wide), 3, 1, None, None, stream) == pd.PD_ERANGE
+    # just inside the limit the call succeeds
+    wide[1, 0] = (1 << 25) - 1
+    cost = torch.empty(3, dtype=torch.float64, device="cuda")
+    assert L.pd_knn_cost_static(_p(wide), 3, 1, _p(cost), None, stream) == pd.PD_OK
+    torch.cuda.synchronize()
+    assert cost[2].item() == 1.0 / 75.0
