@@ -20,6 +20,18 @@ using namespace pd;
 
 namespace pd {
 long long g_launch_count = 0;
+
+int device_sms() {
+    static int cached[64];  // 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int v = __atomic_load_n(&cached[dev], __ATOMIC_RELAXED);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+        return 152;
+    __atomic_store_n(&cached[dev], v, __ATOMIC_RELAXED);
+    return v;
+}
 }
 
 namespace pd {
@@ -477,57 +489,59 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
     int nl = 0;
     CK(cudaMemcpyAsync(&nl, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
+    // the compacted arrays hold the live points only
+    const int64_t cn = nl > 0 ? nl : 1;
     int* newpos;
     ALLOC(newpos, int, g->ng);
     CK(cudaMemsetAsync(newpos, 0xff, g->ng * sizeof(int), g->st));  // -1: not kept
     CK(launch_newpos(list, nl, newpos, g->st));
     int4* pos2;
-    ALLOC(pos2, int4, g->n);
+    ALLOC(pos2, int4, cn);
     CK(launch_take_i4(list, nl, g->pos, pos2, g->st));
     gfree(g, g->pos);
     g->pos = pos2;
     u64* code2;
-    ALLOC(code2, u64, g->n);
+    ALLOC(code2, u64, cn);
     CK(launch_take_u64(list, nl, g->code, code2, g->st));
     gfree(g, g->code);
     g->code = code2;
     if (g->rgb) {
         uchar4* r2;
-        ALLOC(r2, uchar4, g->n);
+        ALLOC(r2, uchar4, cn);
         CK(launch_take_uc4(list, nl, g->rgb, r2, g->st));
         gfree(g, g->rgb);
         g->rgb = r2;
     }
     if (g->nrm) {
         float4* n2;
-        ALLOC(n2, float4, g->n);
+        ALLOC(n2, float4, cn);
         CK(launch_take_f4(list, nl, g->nrm, n2, g->st));
         gfree(g, g->nrm);
         g->nrm = n2;
     }
     if (remap_state) {
         u64* p2;
-        ALLOC(p2, u64, g->n);
+        ALLOC(p2, u64, cn);
         CK(launch_take_u64(list, nl, g->prim, p2, g->st));
         gfree(g, g->prim);
         g->prim = p2;
         u64* r2;
-        ALLOC(r2, u64, g->n);
+        ALLOC(r2, u64, cn);
         CK(launch_take_u64(list, nl, g->rk2, r2, g->st));
         gfree(g, g->rk2);
         g->rk2 = r2;
         uint8_t* f2;
-        ALLOC(f2, uint8_t, g->n);
+        ALLOC(f2, uint8_t, cn);
         CK(launch_take_u8(list, nl, g->flg, f2, g->st));
         gfree(g, g->flg);
         g->flg = f2;
         u64* h2;
-        ALLOC(h2, u64, g->n);
+        ALLOC(h2, u64, cn);
         CK(launch_take_u64(list, nl, g->hz, h2, g->st));
         gfree(g, g->hz);
         g->hz = h2;
         int* nb2;
-        ALLOC(nb2, int, (size_t)g->n * g->S);
+        ALLOC(nb2, int, (size_t)cn * g->S);
         CK(launch_remap(list, nl, g->nbr, nb2, newpos, g->ng, g->S, g->st));
         gfree(g, g->nbr);
         g->nbr = nb2;

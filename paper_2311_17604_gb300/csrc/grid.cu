@@ -40,7 +40,7 @@ cudaError_t launch_bbox(const int32_t* xyz, int64_t n, int* out6, cudaStream_t s
     cudaError_t e = cudaMemcpyAsync(out6, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e) return e;
     int blocks = (int)((n + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sms() * 8) blocks = device_sms() * 8;
     if (blocks < 1) blocks = 1;
     bbox_kernel<<<blocks, 256, 0, st>>>(xyz, n, out6); note_launch();
     return cudaGetLastError();

@@ -617,7 +617,7 @@ static cudaError_t launch_knn_t(const GridView& g, const KnnArgs& a, cudaStream_
     if (a.ngroups <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((a.ngroups + PD_WARPS - 1) / PD_WARPS);
     // list mode: a persistent grid (about 6 resident blocks per SM)
-    if (a.glist && blocks > 152u * 6u) blocks = 152u * 6u;
+    if (a.glist && blocks > (unsigned)device_sms() * 6u) blocks = (unsigned)device_sms() * 6u;
     if (a.glist) {
         if (a.term != 0)
             knn_kernel<S, FILT, true, true><<<blocks, PD_WARPS * 32, 0, st>>>(g, a);

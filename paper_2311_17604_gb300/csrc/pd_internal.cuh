@@ -172,6 +172,10 @@ __device__ inline unsigned long long sqd(int4 a, int4 b) {
 extern long long g_launch_count;
 inline void note_launch() { __atomic_fetch_add(&g_launch_count, 1, __ATOMIC_RELAXED); }
 
+// Streaming multiprocessors of the current device (queried once per device
+// and cached); persistent and grid-stride launches size their grids from it.
+int device_sms();
+
 // ---------------------------------------------------------------- warp utils
 __device__ inline int warp_lane() { return threadIdx.x & 31; }
 

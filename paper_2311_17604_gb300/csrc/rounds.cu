@@ -552,7 +552,7 @@ cudaError_t launch_sel_hist(const u64* prim, const uint8_t* alive, int64_t n, co
     if (e) return e;
     int64_t len = lp ? llen : n;
     int blocks = (int)((len + 255) / 256);
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > device_sms() * 4) blocks = device_sms() * 4;
     if (blocks < 1) blocks = 1;
     sel_hist_kernel<<<blocks, 256, 0, st>>>(prim, alive, n, lp, li, llen, pass, sp, hist); note_launch();
     return cudaGetLastError();
@@ -567,7 +567,7 @@ cudaError_t launch_sel_compact(const u64* prim, const int4* pos, const uint8_t* 
     if (e) return e;
     int64_t len = lp ? llen : n;
     int blocks = (int)((len + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sms() * 8) blocks = device_sms() * 8;
     if (blocks < 1) blocks = 1;
     sel_compact_kernel<<<blocks, 256, 0, st>>>(prim, pos, alive, n, lp, li, llen, pass, sp, op,
                                                oi, ocount); note_launch();
@@ -584,7 +584,7 @@ cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* pr
                                 const uint8_t* alive, const uint8_t* inP, uint8_t* rej,
                                 const u64* lam, const int* nbr, int S, int k, int2* pairs,
                                 int pair_cap, const int* csorted, RoundDev* rd, cudaStream_t st) {
-    danger_kernel<<<152 * DG_BLOCKS_PER_SM, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
+    danger_kernel<<<device_sms() * DG_BLOCKS_PER_SM, DG_WARPS * 32, 0, st>>>(g, src, &rd->nsrc, prim, alive, inP, rej,
                                                      lam, S <= PD_DG_SMAX ? nbr : nullptr, S, k,
                                                      pairs, &rd->npairs, pair_cap, &rd->overflow,
                                                      &rd->cap_over, csorted, &rd->ncs); note_launch();

@@ -16,7 +16,7 @@
 namespace pd {
 
 #define FULLM 0xffffffffu
-#define PERSIST_BLOCKS (152 * 8)
+#define PERSIST_BLOCKS (device_sms() * 8)
 
 // ------------------------------------------------------------------ setup
 __global__ void round_setup_kernel(RoundDev* rd) {
@@ -536,7 +536,7 @@ cudaError_t round_launch_finish(RoundDev* rd, cudaStream_t st) {
 cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
                                 SelBuffers& b, RoundDev* rd, cudaStream_t st) {
     int blocks = (int)((n + 255) / 256);
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > device_sms() * 4) blocks = device_sms() * 4;
     if (blocks < 1) blocks = 1;
     for (int pass = 0; pass < 8; pass++) {
         seld_hist_kernel<<<blocks, 256, 0, st>>>(prim, alive, n, b.p[0], b.i[0], b.p[1], b.i[1],
