@@ -56,6 +56,9 @@ def _load():
             lib.orc_decimate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P, P, P]
             lib.orc_decimate.restype = ctypes.c_int
+            lib.orc_knn_query.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P,
+                                          P, P]
+            lib.orc_knn_query.restype = ctypes.c_int
             lib.orc_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -98,6 +101,25 @@ def knn_cost(xyz, k, live=None, term=TERM_NONE, a=0.0, rgb=None, nrm=None, backe
                               _ptr(d2), _ptr(idx), _ptr(cost))
     if rc != 0:
         raise ValueError("orc_knn_cost: invalid arguments")
+    return d2, idx, cost
+
+
+def knn_query(xyz, queries, k):
+    """Brute-force k nearest neighbours and density cost (Eq. 10/11) of the
+    given query points among all points (every point live).
+
+    Returns (d2 [nq,k] int64 ascending, idx [nq,k] int32, cost [nq] float64).
+    """
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    nq = len(q)
+    d2 = np.empty((nq, k), dtype=np.int64)
+    idx = np.empty((nq, k), dtype=np.int32)
+    cost = np.empty(nq, dtype=np.float64)
+    rc = _load().orc_knn_query(_ptr(xyz), xyz.shape[0], _ptr(q), nq, k, _ptr(d2), _ptr(idx),
+                               _ptr(cost))
+    if rc != 0:
+        raise ValueError("orc_knn_query: invalid arguments")
     return d2, idx, cost
 
 

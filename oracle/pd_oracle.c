@@ -561,6 +561,48 @@ int orc_decimate(const int32_t* xyz, const uint8_t* rgb, const float* nrm, int64
 }
 
 /* Number of threads the parallel loops use (1 without OpenMP). */
+/*
+ * Brute-force k nearest neighbours and density cost (Eq. 10/11, no weights)
+ * of a few query points among all n points (every point live): the
+ * definition, for spot checks of clouds too large for the greedy.
+ *   queries  nq point indices.
+ *   d2_out   nq*k int64, ascending (d^2, index); D2_NONE where missing.
+ *   idx_out  nq*k int32 (-1 where missing).  May be NULL.
+ *   cost_out nq doubles: sum of 1.0 / d_i^2 nearest first (+inf for a
+ *            coincident neighbour).  May be NULL.
+ * Queries run in parallel (each scans all n points).
+ */
+int orc_knn_query(const int32_t* xyz, int64_t n, const int64_t* queries, int64_t nq, int k,
+                  int64_t* d2_out, int32_t* idx_out, double* cost_out) {
+    if (!xyz || n < 0 || n > INT32_MAX || !queries || nq < 0 || k < 1 || k > ORC_KMAX ||
+        !d2_out)
+        return -1;
+    for (int64_t t = 0; t < nq; t++)
+        if (queries[t] < 0 || queries[t] >= n) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nq; t++) {
+        int64_t d2s[ORC_KMAX];
+        int32_t ids[ORC_KMAX];
+        int cnt = 0;
+        const int64_t q = queries[t];
+        const int32_t* qp = xyz + 3 * q;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == q) continue;
+            int64_t d2 = sqdist(qp, xyz + 3 * j);
+            if (cnt == k && d2 > d2s[k - 1]) continue;
+            topk_insert(d2s, ids, &cnt, k, d2, (int32_t)j);
+        }
+        double c = 0.0;
+        for (int i = 0; i < k; i++) {
+            d2_out[t * k + i] = i < cnt ? d2s[i] : D2_NONE;
+            if (idx_out) idx_out[t * k + i] = i < cnt ? ids[i] : -1;
+            if (i < cnt) c = c + 1.0 / (double)d2s[i];
+        }
+        if (cost_out) cost_out[t] = c;
+    }
+    return 0;
+}
+
 int orc_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -10,7 +10,10 @@ paper motivates its method with exactly this pattern (Introduction, Fig. 1).
 
 Point order is the acquisition order: index = azimuth_step * n_el + elev_step
 (after ray dropout the survivors keep their relative order).  Every random
-number comes from numpy's PCG64 with an explicit seed.
+number comes from numpy's PCG64 with an explicit seed, except the range noise
+of the site scan: its compiled ray caster (synth_site.c) draws it from
+splitmix64 keyed by (seed, station, ray) so that a billion rays can be cast on
+all host cores with a result independent of the thread count.
 
 Generators
 ----------
@@ -319,64 +322,122 @@ def outdoor_scan(seed: int = 0, n_az: int = 10000, n_el: int = 2000,
                              "n_el": n_el, "dropout": dropout, "max_range": max_range})
 
 
-def site_scan(seed: int = 0, stations: int = 40, n_az: int = 10000, n_el: int = 2500,
-              size=(200.0, 200.0, 30.0), noise_mm: float = 2.0, rgb: bool = True,
-              station_ids=None) -> Scan:
-    """Merged multi-station scan of a closed site (ground, walls, roof, objects).
-
-    Every station stands 1.5 m above the ground at a random position; the site
-    is closed so every ray returns.  Stations are concatenated in order.
-    ``station_ids`` selects a subset of stations (for bounded samples).
-    """
+def _site_scene(seed, stations, size):
+    """Primitives and station positions of the site (numpy PCG64, seeded)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     W, Dp, H = (float(v) for v in size)
-    prims = [{"fn": (lambda o, D: _hit_box_inside(o, D, np.zeros(3), np.array([W, Dp, H]))),
-              "rgb": _colour(rng)}]
+    site_rgb = _colour(rng)
+    prims = []
     for _ in range(30):  # boxes (buildings, containers)
         w = rng.uniform(2.0, 25.0, size=2)
         h = rng.uniform(2.0, 20.0)
         x0 = rng.uniform(2.0, W - w[0] - 2.0)
         y0 = rng.uniform(2.0, Dp - w[1] - 2.0)
         lo, hi = np.array([x0, y0, 0.0]), np.array([x0 + w[0], y0 + w[1], h])
-        prims.append({"fn": (lambda o, D, lo=lo, hi=hi: _hit_box_outside(o, D, lo, hi)),
-                      "rgb": _colour(rng), "box": (lo, hi), "bc": (lo + hi)[:2] / 2,
+        prims.append({"box": (lo, hi), "rgb": _colour(rng), "bc": (lo + hi)[:2] / 2,
                       "br": float(np.linalg.norm(hi[:2] - lo[:2]) / 2)})
     for _ in range(30):  # cylinders (columns, tanks, poles)
         r = rng.uniform(0.15, 3.0)
         cx, cy = rng.uniform(5.0, W - 5.0), rng.uniform(5.0, Dp - 5.0)
         h = rng.uniform(2.0, 25.0)
-        prims.append({"fn": (lambda o, D, cx=cx, cy=cy, r=r, h=h:
-                             _hit_cylinder_z(o, D, cx, cy, r, 0.0, h)),
-                      "rgb": _colour(rng), "cyl": (cx, cy, r), "bc": np.array([cx, cy]),
+        prims.append({"cyl": (cx, cy, r, h), "rgb": _colour(rng), "bc": np.array([cx, cy]),
                       "br": r})
     pos = []
     while len(pos) < stations:
         p = np.array([rng.uniform(3.0, W - 3.0), rng.uniform(3.0, Dp - 3.0), 1.5])
         inside = False
-        for pr in prims[1:]:
+        for pr in prims:
             if "box" in pr:
                 lo, hi = pr["box"]
                 if np.all(p >= lo - 0.5) and np.all(p <= hi + 0.5):
                     inside = True
             else:
-                cx, cy, r = pr["cyl"]
+                cx, cy, r, _ = pr["cyl"]
                 if math.hypot(p[0] - cx, p[1] - cy) < r + 0.5:
                     inside = True
         if not inside:
             pos.append(p)
-    ids = range(stations) if station_ids is None else station_ids
-    xs, cs = [], []
-    for sid in ids:
-        noise_rng = np.random.Generator(np.random.PCG64([seed, 100 + int(sid)]))
-        xyz, c, _ = _trace(pos[sid], prims, n_az, n_el, noise_rng, noise_mm * 1e-3, 0.0,
-                           _INF, rgb, False)
-        xs.append(xyz)
-        if rgb:
-            cs.append(c)
-    xyz = np.ascontiguousarray(np.concatenate(xs))
-    c = np.ascontiguousarray(np.concatenate(cs)) if rgb else None
-    return Scan(xyz, c, None, {"scene": "site", "seed": seed, "stations": list(ids),
-                               "n_az": n_az, "n_el": n_el})
+    return prims, pos, site_rgb
+
+
+_SYNTH_LIB = None
+
+
+def _synth_lib():
+    """The compiled site ray caster (synth_site.c, built with gcc on first use)."""
+    global _SYNTH_LIB
+    if _SYNTH_LIB is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "synth_site.c")
+        lib = os.path.join(here, "libsynth.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + ".%d.tmp" % os.getpid()
+            subprocess.run(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off",
+                            "-fno-fast-math", "-fPIC", "-shared", src, "-o", tmp, "-lm"],
+                           check=True)
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        P = ctypes.c_void_p
+        L.synth_site.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_double, ctypes.c_uint64, P, P, P]
+        L.synth_site.restype = ctypes.c_int
+        L.synth_threads.restype = ctypes.c_int
+        _SYNTH_LIB = L
+    return _SYNTH_LIB
+
+
+def site_scan(seed: int = 0, stations: int = 40, n_az: int = 10000, n_el: int = 2500,
+              size=(200.0, 200.0, 30.0), noise_mm: float = 2.0, rgb: bool = True,
+              station_ids=None) -> Scan:
+    """Merged multi-station scan of a closed site (ground, walls, roof, objects).
+
+    The site is the inside of a W x D x H box with 30 axis-aligned boxes (2-25 m
+    footprint, 2-20 m high) and 30 vertical cylinders (radius 0.15-3 m, 2-25 m
+    high).  Every station stands 1.5 m above the ground at a random position
+    outside every object; the site is closed, so every ray returns and each
+    station gives exactly n_az * n_el points.  Stations are concatenated in
+    order, so points of different stations on the same surface interleave as
+    near-duplicates.  ``station_ids`` selects a subset of the stations (for
+    bounded samples).  The rays are cast by the compiled ray caster
+    (synth_site.c, all host cores); its range noise is seeded per (seed,
+    station, ray), so the output does not depend on the thread count.
+    """
+    import ctypes
+    prims, pos, site_rgb = _site_scene(seed, stations, size)
+    ids = list(range(stations)) if station_ids is None else [int(i) for i in station_ids]
+    rec = np.zeros((len(prims), 17), dtype=np.float64)
+    for q, pr in enumerate(prims):
+        if "box" in pr:
+            lo, hi = pr["box"]
+            rec[q, 0] = 0
+            rec[q, 1:4], rec[q, 4:7] = lo, hi
+        else:
+            cx, cy, r, h = pr["cyl"]
+            rec[q, 0] = 1
+            rec[q, 7:11] = (cx, cy, r, h)
+        rec[q, 11:13] = pr["bc"]
+        rec[q, 13] = pr["br"]
+        rec[q, 14:17] = pr["rgb"]
+    st = np.ascontiguousarray(np.stack([pos[i] for i in ids]), dtype=np.float64)
+    sid = np.asarray(ids, dtype=np.int64)
+    sz = np.asarray(size, dtype=np.float64)
+    srgb = np.asarray(site_rgb, dtype=np.float64)
+    n = len(ids) * n_az * n_el
+    xyz = np.empty((n, 3), dtype=np.int32)
+    col = np.empty((n, 3), dtype=np.uint8) if rgb else None
+    P = ctypes.c_void_p
+    rc = _synth_lib().synth_site(rec.ctypes.data_as(P), len(prims), sz.ctypes.data_as(P),
+                                 st.ctypes.data_as(P), sid.ctypes.data_as(P), len(ids), n_az,
+                                 n_el, noise_mm * 1e-3, int(seed),
+                                 srgb.ctypes.data_as(P), xyz.ctypes.data_as(P),
+                                 None if col is None else col.ctypes.data_as(P))
+    if rc != 0:
+        raise RuntimeError("synth_site failed (%d)" % rc)
+    return Scan(xyz, col, None, {"scene": "site", "seed": seed, "stations": ids,
+                                 "n_az": n_az, "n_el": n_el})
 
 
 def batch_specs(seed: int = 0, count: int = 512, n_lo: float = 5e4, n_hi: float = 5e6,

@@ -231,3 +231,15 @@ def test_kdtree_equals_brute(orc, shape, k):
     ka = orc.decimate(x, k, 400, backend=orc.BRUTE)
     kb = orc.decimate(x, k, 400, backend=orc.KDTREE)
     assert np.array_equal(ka, kb)
+
+
+def test_knn_query_equals_full_brute_force(orc):
+    """The query-subset brute force (spot checks of huge clouds) returns the
+    rows of the full brute-force pass: same d^2 lists, indices and costs."""
+    x = synth.random_cloud(11, 3000, 40)  # duplicates and ties
+    q = np.arange(0, 3000, 37)
+    for k in (1, 4, 16):
+        d2, idx, cost = orc.knn_cost(x, k, backend=orc.BRUTE)
+        qd2, qidx, qcost = orc.knn_query(x, q, k)
+        assert np.array_equal(qd2, d2[q]) and np.array_equal(qidx, idx[q])
+        assert np.array_equal(qcost.view(np.int64), cost[q].view(np.int64))
