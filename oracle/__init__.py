@@ -59,6 +59,8 @@ def _load():
             lib.orc_knn_query.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P,
                                           P, P]
             lib.orc_knn_query.restype = ctypes.c_int
+            lib.orc_radius_counts.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, P]
+            lib.orc_radius_counts.restype = ctypes.c_int
             lib.orc_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -121,6 +123,18 @@ def knn_query(xyz, queries, k):
     if rc != 0:
         raise ValueError("orc_knn_query: invalid arguments")
     return d2, idx, cost
+
+
+def radius_counts(xyz, radii_mm):
+    """counts[p, j] = #{q != p : d(p,q)^2 <= r_j^2} by brute force (int64)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    r2 = np.ascontiguousarray(np.asarray(radii_mm, dtype=np.int64) ** 2)
+    n, nr = xyz.shape[0], len(r2)
+    counts = np.empty((n, nr), dtype=np.int64)
+    rc = _load().orc_radius_counts(_ptr(xyz), n, _ptr(r2), nr, _ptr(counts))
+    if rc != 0:
+        raise ValueError("orc_radius_counts: invalid arguments")
+    return counts
 
 
 def decimate(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None, backend=KDTREE,

@@ -603,6 +603,28 @@ int orc_knn_query(const int32_t* xyz, int64_t n, const int64_t* queries, int64_t
     return 0;
 }
 
+/*
+ * Neighbour counts of the quality report (section "Results and Discussion",
+ * the cube experiment): for every point p and radius r_j,
+ *     counts[p * nr + j] = #{q != p : d(p,q)^2 <= r2[j]}
+ * by brute force over all n points (exact int64 squared distances).
+ */
+int orc_radius_counts(const int32_t* xyz, int64_t n, const int64_t* r2, int nr,
+                      int64_t* counts) {
+    if (!xyz || n < 0 || !r2 || nr < 1 || !counts) return -1;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < n; p++) {
+        for (int j = 0; j < nr; j++) counts[p * nr + j] = 0;
+        for (int64_t q = 0; q < n; q++) {
+            if (q == p) continue;
+            int64_t d2 = sqdist(xyz + 3 * p, xyz + 3 * q);
+            for (int j = 0; j < nr; j++)
+                if (d2 <= r2[j]) counts[p * nr + j]++;
+        }
+    }
+    return 0;
+}
+
 int orc_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI of libpd (pd.h): contexts, grids, decimation driver.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -13,6 +14,7 @@
 
 #include "../../include/pd.h"
 #include "../../include/pd_normals.h"
+#include "../../include/pd_quality.h"
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
 
@@ -1229,6 +1231,235 @@ int grid_knn16(pd_grid* g, cudaStream_t st, GridNbrs* out) {
     return PD_OK;
 }
 }  // namespace pd
+
+// ============================================================ API: quality report
+namespace {
+struct CtxScratch {
+    pd_ctx* c;
+    cudaStream_t st;
+};
+void* cs_alloc(void* self, size_t bytes) {
+    CtxScratch* x = (CtxScratch*)self;
+    return ctx_alloc(x->c, bytes, x->st);
+}
+void cs_free(void* self, void* p) {
+    CtxScratch* x = (CtxScratch*)self;
+    ctx_free(x->c, p, x->st);
+}
+}  // namespace
+
+static_assert(PD_QUALITY_MAX_RADII == PD_QUALITY_MAXR, "radius limit");
+
+extern "C" int pd_quality_report(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t* keep_dev,
+                                 int64_t n, const int32_t* radii_mm, int nr, pd_quality* out,
+                                 void* stream) {
+    if (!ctx || !xyz_dev || !radii_mm || !out || n < 1 || n >= (1ll << 31) - 64 || nr < 1 ||
+        nr > PD_QUALITY_MAX_RADII) {
+        if (ctx) set_err(ctx, "pd_quality_report: invalid argument%s (nr = %lld)", "", nr);
+        return PD_EINVAL;
+    }
+    for (int j = 0; j < nr; j++) {
+        if (radii_mm[j] < 1 || radii_mm[j] > (1 << 24) || (j && radii_mm[j] <= radii_mm[j - 1])) {
+            set_err(ctx, "pd_quality_report: radii must ascend strictly in [1, 2^24] mm%s (%lld)",
+                    "", j);
+            return PD_EINVAL;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    memset(out, 0, sizeof(*out));
+    out->nr = nr;
+    for (int j = 0; j < nr; j++) out->radius_mm[j] = radii_mm[j];
+    CtxScratch cs = {ctx, st};
+    Scratch sc;
+    sc.alloc = cs_alloc;
+    sc.free = cs_free;
+    sc.self = &cs;
+    std::vector<void*> owned;
+    auto get = [&](size_t bytes) {
+        void* p = ctx_alloc(ctx, bytes, st);
+        if (p) owned.push_back(p);
+        return p;
+    };
+    pd_grid* g = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, c0 = nullptr, c1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&c0);
+    cudaEventCreate(&c1);
+    auto body = [&]() -> int {
+#define QCK(x)                                                                     \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess) {                                                   \
+            set_err(ctx, "pd_quality_report: CUDA error at %s (%lld)", #x, (long long)e_); \
+            return e_ == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA;         \
+        }                                                                          \
+    } while (0)
+#define QGET(ptr, type, count)                                                     \
+    do {                                                                           \
+        ptr = (type*)get(sizeof(type) * (size_t)(count));                          \
+        if (!ptr) {                                                                \
+            set_err(ctx, "pd_quality_report: allocation of %s failed (%lld)", #ptr, \
+                    (long long)(count));                                   \
+            return PD_ENOMEM;                                                      \
+        }                                                                          \
+    } while (0)
+        QCK(cudaEventRecord(e0, st));
+        // the retained points, in input order
+        const int32_t* xyz = xyz_dev;
+        int64_t P = n;
+        if (keep_dev) {
+            int* list;
+            int* cnt;
+            QGET(list, int, n);
+            QGET(cnt, int, 1);
+            QCK(stable_compact(keep_dev, n, list, cnt, sc, st));
+            int hp = 0;
+            QCK(cudaMemcpyAsync(&hp, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QCK(cudaStreamSynchronize(st));
+            P = hp;
+            if (P > 0) {
+                int32_t* kx;
+                QGET(kx, int32_t, 3 * P);
+                QCK(launch_take_xyz(list, cnt, P, xyz_dev, kx, st));
+                xyz = kx;
+            }
+        }
+        out->points = P;
+        out->min_spacing2_mm2 = -1;
+        if (P == 0) return PD_OK;
+        pd_grid_params gp;
+        memset(&gp, 0, sizeof(gp));
+        gp.leaf_max = 32;
+        int rc = pd_build_grid(ctx, xyz, nullptr, P, &gp, stream, &g);
+        if (rc) return rc;
+        // Eq. 2: nearest-neighbour spacing of the retained points (k = 1 search)
+        if (P >= 2) {
+            pd_cost_params cp;
+            memset(&cp, 0, sizeof(cp));
+            cp.k = 1;
+            rc = prepare_state(g, &cp);
+            if (rc) return rc;
+            rc = knn_all(g, &cp, nullptr);
+            if (rc) return rc;
+            const int64_t nb = (P + 255) / 256;
+            u64* bmin;
+            double* bsum;
+            QGET(bmin, u64, nb);
+            QGET(bsum, double, nb);
+            QCK(launch_spacing(g->rk2, P, bmin, bsum, st));
+            std::vector<u64> hmin(nb);
+            std::vector<double> hsum(nb);
+            QCK(cudaMemcpyAsync(hmin.data(), bmin, nb * sizeof(u64), cudaMemcpyDeviceToHost, st));
+            QCK(cudaMemcpyAsync(hsum.data(), bsum, nb * sizeof(double), cudaMemcpyDeviceToHost,
+                                st));
+            QCK(cudaStreamSynchronize(st));
+            u64 mn = ~0ull;
+            double sum = 0.0;
+            for (int64_t b = 0; b < nb; b++) {
+                mn = std::min(mn, hmin[b]);
+                sum = sum + hsum[b];
+            }
+            out->min_spacing2_mm2 = (int64_t)mn;
+            out->mean_spacing_mm = sum / (double)P;
+        }
+        // neighbour counts within each radius: cells whose edge reaches r_max
+        int L = 0;
+        while (L < g->B && (1ll << (L + g->shift)) < (long long)radii_mm[nr - 1]) L++;
+        const int H = PD_QUALITY_HIST;
+        u64 *r2, *sn, *sn2;
+        uint32_t* hist;
+        QGET(r2, u64, nr);
+        QGET(sn, u64, nr);
+        QGET(sn2, u64, nr);
+        QGET(hist, uint32_t, (size_t)nr * H);
+        std::vector<u64> hr2(nr);
+        for (int j = 0; j < nr; j++) hr2[j] = (u64)radii_mm[j] * (u64)radii_mm[j];
+        QCK(cudaMemcpyAsync(r2, hr2.data(), nr * sizeof(u64), cudaMemcpyHostToDevice, st));
+        QCK(cudaMemsetAsync(sn, 0, nr * sizeof(u64), st));
+        QCK(cudaMemsetAsync(sn2, 0, nr * sizeof(u64), st));
+        QCK(cudaMemsetAsync(hist, 0, (size_t)nr * H * sizeof(uint32_t), st));
+        QCK(cudaEventRecord(c0, st));
+        QCK(launch_radius_counts(view_of(g), P, L, r2, nr, sn, sn2, hist, H, st));
+        QCK(cudaEventRecord(c1, st));
+        std::vector<u64> T(nr), U(nr);
+        std::vector<uint32_t> hh((size_t)nr * H);
+        QCK(cudaMemcpyAsync(T.data(), sn, nr * sizeof(u64), cudaMemcpyDeviceToHost, st));
+        QCK(cudaMemcpyAsync(U.data(), sn2, nr * sizeof(u64), cudaMemcpyDeviceToHost, st));
+        QCK(cudaMemcpyAsync(hh.data(), hist, (size_t)nr * H * sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, st));
+        QCK(cudaEventRecord(e1, st));
+        QCK(cudaStreamSynchronize(st));
+        // fractiles: the smallest v with #{N <= v} >= ceil(f P)
+        static const int kFrac[PD_QUALITY_NFRAC] = {1, 10, 25, 50, 75, 90, 99};
+        for (int j = 0; j < nr; j++) {
+            out->mean[j] = (double)T[j] / (double)P;
+            const uint32_t* hj = &hh[(size_t)j * H];
+            out->count_clipped += hj[H - 1];
+            for (int f = 0; f < PD_QUALITY_NFRAC; f++) {
+                int64_t rank = (kFrac[f] * P + 99) / 100;
+                if (rank < 1) rank = 1;
+                int64_t cum = 0;
+                int v = 0;
+                for (; v < H; v++) {
+                    cum += hj[v];
+                    if (cum >= rank) break;
+                }
+                out->fractile[j][f] = v < H ? v : H - 1;
+            }
+        }
+        // least squares of y = N_j(p) on x = pi r_j^2 (m^2) over the P * nr samples
+        std::vector<double> x(nr);
+        double xs = 0.0;
+        for (int j = 0; j < nr; j++) {
+            double r = (double)radii_mm[j] / 1000.0;
+            x[j] = 3.141592653589793 * r * r;
+            xs = xs + x[j];
+        }
+        const double xbar = xs / (double)nr;
+        double varx = 0.0, cov = 0.0;
+        unsigned __int128 sy = 0, suu = 0;
+        for (int j = 0; j < nr; j++) {
+            double dx = x[j] - xbar;
+            varx = varx + dx * dx;
+            cov = cov + dx * (double)T[j];
+            sy += T[j];
+            suu += U[j];
+        }
+        varx = varx * (double)P;   // sum over all samples of (x - xbar)^2
+        const unsigned __int128 N = (unsigned __int128)P * (unsigned __int128)nr;
+        // N * sum (y - ybar)^2 = N * sum y^2 - (sum y)^2, exact in 128 bits
+        const unsigned __int128 nss = N * suu - sy * sy;
+        const double sstot = (double)nss / (double)N;
+        if (nr >= 2 && varx > 0.0) {
+            out->slope_per_m2 = cov / varx;
+            out->intercept = (double)sy / (double)N - out->slope_per_m2 * xbar;
+            double ssres = sstot - cov * cov / varx;
+            if (ssres < 0.0) ssres = 0.0;
+            out->r2 = sstot > 0.0 ? cov * cov / (varx * sstot) : 1.0;
+            out->rmse = sqrt(ssres / (double)N);
+        } else {
+            out->slope_per_m2 = out->intercept = out->r2 = out->rmse = NAN;
+        }
+        float ms = 0.f, mc = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventElapsedTime(&mc, c0, c1);
+        out->ms = ms;
+        out->ms_counts = mc;
+        return PD_OK;
+#undef QCK
+#undef QGET
+    };
+    int rc = body();
+    if (g) pd_grid_free(g);
+    for (void* p : owned) ctx_free(ctx, p, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(c0);
+    cudaEventDestroy(c1);
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = PD_ECUDA;
+    return rc;
+}
 
 // ============================================================ API: batch
 // Many independent scans through a fixed number of concurrent slots: every

@@ -46,6 +46,21 @@ cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* 
 cudaError_t stable_compact(const uint8_t* flag, int64_t n, int* out, int* count,
                            const Scratch& s, cudaStream_t st);
 
+// ---------------------------------------------------------------- quality.cu
+#define PD_QUALITY_MAXR 32
+// Per retained point (grid order): neighbour counts within each radius (r2:
+// ascending squared radii, nr <= PD_QUALITY_MAXR) over the 3x3x3 cells of
+// level L (cell edge >= the largest radius); per radius the sums of N and
+// N^2 and a histogram of N with H bins (the top bin holds N >= H - 1).
+cudaError_t launch_radius_counts(const GridView& g, int64_t n, int L, const u64* r2, int nr,
+                                 u64* sum_n, u64* sum_n2, uint32_t* hist, int H,
+                                 cudaStream_t st);
+// Per block of 256 points: least nearest squared distance and sum of sqrt.
+cudaError_t launch_spacing(const u64* rk2, int64_t n, u64* bmin, double* bsum, cudaStream_t st);
+// out[t] = xyz row list[t] for t < *count (cap >= *count rows are reserved).
+cudaError_t launch_take_xyz(const int* list, const int* count, int64_t cap, const int32_t* xyz,
+                            int32_t* out, cudaStream_t st);
+
 // ---------------------------------------------------------------- round state
 #define PD_FIX_ITERS 8
 

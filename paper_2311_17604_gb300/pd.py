@@ -30,7 +30,9 @@ EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "
             "pd_normals_mlp",
             # pd_serve.h
             "pd_serve_open", "pd_serve_submit", "pd_serve_poll", "pd_serve_counts",
-            "pd_serve_close"]
+            "pd_serve_close",
+            # pd_quality.h
+            "pd_quality_report"]
 PD_NORMAL_K, PD_MLP_IN, PD_MLP_HIDDEN = 16, 48, 64
 PD_NORMAL_DEFINED, PD_NORMAL_PLANAR = 1, 2
 PD_SERVE_BYTES_PER_POINT, PD_SERVE_BYTES_PER_POINT_NORMALS = 240, 400
@@ -100,6 +102,32 @@ class pd_serve_result(ctypes.Structure):
                 ("stats", pd_stats)]
 
 
+PD_QUALITY_MAX_RADII, PD_QUALITY_NFRAC, PD_QUALITY_HIST = 32, 7, 16384
+QUALITY_FRACTILES = (1, 10, 25, 50, 75, 90, 99)  # percent
+
+
+class pd_quality(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("nr", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("radius_mm", ctypes.c_int32 * PD_QUALITY_MAX_RADII),
+                ("mean", ctypes.c_double * PD_QUALITY_MAX_RADII),
+                ("fractile", (ctypes.c_int32 * PD_QUALITY_NFRAC) * PD_QUALITY_MAX_RADII),
+                ("slope_per_m2", ctypes.c_double), ("intercept", ctypes.c_double),
+                ("r2", ctypes.c_double), ("rmse", ctypes.c_double),
+                ("min_spacing2_mm2", ctypes.c_int64), ("mean_spacing_mm", ctypes.c_double),
+                ("count_clipped", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("ms_counts", ctypes.c_double), ("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self):
+        nr = self.nr
+        return {"points": self.points, "radius_mm": list(self.radius_mm[:nr]),
+                "mean": list(self.mean[:nr]),
+                "fractile": [list(self.fractile[j]) for j in range(nr)],
+                "slope_per_m2": self.slope_per_m2, "intercept": self.intercept, "r2": self.r2,
+                "rmse": self.rmse, "min_spacing2_mm2": self.min_spacing2_mm2,
+                "mean_spacing_mm": self.mean_spacing_mm, "count_clipped": self.count_clipped,
+                "ms": self.ms, "ms_counts": self.ms_counts}
+
+
 class pd_train_params(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("seed", ctypes.c_uint64)]
@@ -147,6 +175,8 @@ def lib():
         L.pd_serve_counts.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                       ctypes.POINTER(I64)]
         L.pd_serve_close.argtypes = [P]
+        L.pd_quality_report.argtypes = [P, P, P, I64, P, ctypes.c_int,
+                                        ctypes.POINTER(pd_quality), P]
         for f in EXPORTED:
             if f not in ("pd_ctx_destroy", "pd_strerror", "pd_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -345,6 +375,24 @@ def pd_autotune(ctx: Context, xyz, ratio, k=1, term=PD_TERM_NONE, weight=0.0, no
                            float(ratio), int(sample), _stream_ptr(stream), ctypes.byref(out))
     ctx.check(rc, "pd_autotune")
     return int(out.value)
+
+
+def pd_quality_report(ctx: Context, xyz, keep, radii_mm, stream=None):
+    """Quality report (neighbour count against area, fractile bands,
+    regression slope / R^2 / RMSE, Eq. 2 spacing) of the retained points of a
+    device int32 [n,3] cloud; keep: device uint8 [n] or None (all points)."""
+    torch = _torch()
+    assert xyz.is_cuda and xyz.dtype == torch.int32 and xyz.dim() == 2 and xyz.shape[1] == 3
+    xyz = xyz.contiguous()
+    if keep is not None:
+        assert keep.is_cuda and keep.dtype == torch.uint8 and keep.numel() == xyz.shape[0]
+        keep = keep.contiguous()
+    r = np.ascontiguousarray(np.asarray(radii_mm, dtype=np.int32))
+    out = pd_quality()
+    rc = lib().pd_quality_report(ctx.h, _ptr(xyz), _ptr(keep), int(xyz.shape[0]), _ptr(r),
+                                 len(r), ctypes.byref(out), _stream_ptr(stream))
+    ctx.check(rc, "pd_quality_report")
+    return out.as_dict()
 
 
 def pd_knn_cost_static(xyz, k=1, cost=None, knn=None, stream=None):
