@@ -1,7 +1,7 @@
-"""Full-size checks on the benchmark's own workload (needs a GPU).
+"""Full-size checks on the 10.4M-point outdoor workload (needs a GPU).
 
-The outdoor scan of the benchmark (10,000 x 2,000 rays, 10.4M points, k = 4,
-keep 10 %) is too large for the oracle's greedy.  Checked here instead, in the
+The outdoor scan (10,000 x 2,000 rays, 10.4M points, k = 4, keep 10 %) is
+too large for the oracle's greedy inside a test run.  Checked here instead, in the
 launch configuration the benchmark times (the autotuned leaf capacity):
 
   * the k = 4 costs of sampled points against a brute-force search over all
@@ -9,7 +9,10 @@ launch configuration the benchmark times (the autotuned leaf capacity):
     summed nearest first in binary64), bit for bit;
   * the decimation keeps exactly m = floor(0.1 n) points, and gives the same
     keep mask at the autotuned capacity and at capacity 32 (the result may
-    not depend on the cell size).
+    not depend on the cell size);
+  * the whole keep mask equals the oracle's sequential greedy, stored as a
+    SHA-256 digest by tests/golden/make_outdoor_golden.py (the oracle needs
+    about 5 minutes for it, too long for a test run).
 """
 import numpy as np
 import pytest
@@ -75,3 +78,34 @@ def test_decimation_count_and_cell_size_invariance(pd, scan):
     assert int(keeps[0].sum()) == m
     assert np.array_equal(keeps[0], keeps[1])
     ctx.close()
+
+
+def _golden(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = v
+    return out
+
+
+def test_full_keep_mask_equals_oracle_golden(pd, scan):
+    """The whole 10.4M-point keep mask against the oracle's sequential greedy,
+    stored as a digest by tests/golden/make_outdoor_golden.py (oracle only)."""
+    import hashlib
+    gold = _golden("outdoor_k4_keep10.txt")
+    xsha = hashlib.sha256(np.ascontiguousarray(scan.xyz).tobytes()).hexdigest()
+    assert xsha == gold["xyz_sha256"], "the generator's scan differs from the golden's input"
+    assert scan.n == int(gold["n"])
+    m = int(gold["m"])
+    assert m == oracle.target_count(scan.n, 0.1)
+    ctx = pd.Context()
+    xd = torch.from_numpy(scan.xyz).cuda()
+    leaf = pd.pd_autotune(ctx, xd, 0.1, k=4, sample=2_000_000)
+    g = pd.Grid(ctx, xd, leaf_max=leaf)
+    keep = pd.pd_decimate_count(g, m, k=4).cpu().numpy()
+    g.free()
+    ctx.close()
+    assert hashlib.sha256(keep.astype(np.uint8).tobytes()).hexdigest() == gold["keep_sha256"]
