@@ -109,7 +109,7 @@ typedef struct {
     double ms_danger;         /* of rules: k >= 2 danger-pair analysis */
     int64_t pairs_first;      /* (query, candidate) pairs the first pass scanned */
     int32_t leaf_max;         /* the grid's octree leaf capacity */
-    int32_t reserved_stats;
+    int32_t iterations;       /* pd_decimate_wup: cost-update iterations (0 otherwise) */
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */
@@ -154,6 +154,34 @@ int pd_decimate_count(pd_grid* grid, const pd_cost_params* cp, int64_t m, uint8_
 /* Same with m = floor(ratio * n) computed in binary64 (lambda = m / |C|). */
 int pd_decimate_ratio(pd_grid* grid, const pd_cost_params* cp, double ratio, uint8_t* keep_dev,
                       void* stream);
+/*
+ * The paper's own iterative scheme (section "Sub-sampling algorithm"), an
+ * alternative to the exact greedy: not the sequential greedy's result, but
+ * fewer, larger passes.  Until m points remain, each iteration
+ *   1. recomputes the S = 8 nearest neighbours (the extended k+b
+ *      neighbourhood, equal distances ordered by input index) and the
+ *      density cost (Eq. 10 / 11) of every live point;
+ *   2. takes w_up = the m-th smallest key (cost, input index);
+ *   3. removes points above w_up in rounds: a clean live point above w_up
+ *      is removed when no other such point adjacent to it has a larger key
+ *      (adjacent: one of the two lies among the first k stored neighbours of
+ *      the other).  Removed points leave their reverse neighbours' stored
+ *      lists; a point with at least k stored neighbours left takes its cost
+ *      from the first k of them, one with fewer is dirty (not removed) until
+ *      the next iteration.
+ * The paper removes the points above w_up in a sequential sweep over its
+ * voxels; here every round removes, at once, the points no larger-key
+ * candidate interacts with.  Removals never raise a cost, so the count never
+ * drops below m, and every round of every iteration's start removes at least
+ * the largest key.
+ *   cp        density cost (term PD_TERM_NONE), k in [1, 6].
+ *   keep_dev  n bytes: 1 = retained (exactly m ones), input order.
+ * The grid is consumed.  pd_grid_stats reports iterations and rounds.
+ * Reads one counter per round back to the host (a synchronisation).
+ */
+int pd_decimate_wup(pd_grid* grid, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev,
+                    void* stream);
+
 /*
  * Autotuner for the octree leaf capacity (the cell size of the neighbour
  * search).  The paper picks its voxel size by hand (section "Sub-sampling

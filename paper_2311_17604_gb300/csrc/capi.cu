@@ -46,8 +46,8 @@ cudaError_t launch_sel_hist(const u64*, const uint8_t*, int64_t, const u64*, con
 cudaError_t launch_sel_compact(const u64*, const int4*, const uint8_t*, int64_t, const u64*,
                                const int*, int64_t, int, const uint32_t*, u64*, int*, int*,
                                cudaStream_t);
-cudaError_t launch_k1_fix(const int*, const int*, int, const int4*, const int*, int,
-                          const uint8_t*, uint8_t*, int*, cudaStream_t);
+cudaError_t launch_k1_fix(const int*, const int*, int, const int4*, const int*, const uint8_t*,
+                          int, const uint8_t*, uint8_t*, int*, cudaStream_t);
 cudaError_t launch_accept_above(const u64*, const int4*, const uint8_t*, int64_t, u64, int,
                                 uint8_t*, int*, int*, cudaStream_t);
 cudaError_t launch_pair_fix(const int2*, const int*, int, int, const uint8_t*, uint8_t*, int*,
@@ -197,7 +197,7 @@ void gfree(pd_grid* g, void* p) { ctx_free(g->ctx, p, g->st); }
 
 // S = stored neighbours per point for a cost with k neighbours
 int width_for(int k, int density_k1) {
-    if (density_k1) return 8;  // the nearest-distance shell
+    if (density_k1) return 8;  // the 8 nearest: the shell plus spares (k+b buffer)
     if (k <= 6) return 8;      // k nearest + at least 2 spare (k+b buffer)
     return 17;
 }
@@ -701,8 +701,8 @@ int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint
         for (int it = 0; it < 1000000; it++) {
             CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
             if (g->density_k1)
-                CK(launch_k1_fix(cand, &rd->ncand, h.ncand, g->pos, g->nbr, g->S, inP, rej,
-                                 d + 6, g->st));
+                CK(launch_k1_fix(cand, &rd->ncand, h.ncand, g->pos, g->nbr, g->flg, g->S, inP,
+                                 rej, d + 6, g->st));
             else
                 CK(launch_pair_fix(pairs, &rd->npairs, std::min(h.npairs, pair_cap), pair_cap,
                                    inP, rej, d + 6, g->st));
@@ -862,6 +862,12 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         RALLOC(fprim, u64, cap);
         RALLOC(lam, u64, cap);
         pair_cap = (int)std::min<int64_t>(std::max<int64_t>(cap * 4, 1 << 16), 1 << 30);
+        // diagnostic: a smaller danger-pair capacity forces the host settle of
+        // overflowing rounds (the result does not change, only the rounds)
+        if (getenv("PD_PAIR_CAP")) {
+            int v = atoi(getenv("PD_PAIR_CAP"));
+            if (v >= 1 && v < pair_cap) pair_cap = v;
+        }
         RALLOC(pairs, int2, pair_cap);
         ALLOC(g->cmin, u64, (cap + 31) / 32 + 1);
     }
@@ -930,7 +936,11 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
         }
         CK(round_launch_remove(cand, inP, rej, g->alive, rd, g->st));
-        if (use_buf) {
+        if (g->density_k1) {
+            // absorb removals in the stored 8 nearest; search where the new
+            // nearest shell may be incomplete
+            CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
+        } else if (use_buf) {
             // absorb removals in the k+b buffers; search only where < k remain
             CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
         } else {
@@ -950,7 +960,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             int64_t removed = 0;
             rc = settle_round(g, rd, h, inP, rej, cand, pairs, pair_cap, &removed);
             if (rc) return rc;
-            if (use_buf)
+            if (g->density_k1)
+                CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
+            else if (use_buf)
                 CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
             else
                 CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
@@ -1005,6 +1017,124 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
 
 }  // namespace
 
+// The paper's iterative w_up scheme with parallel removal rounds (wup.cu).
+static int wup_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev) {
+    if (!cp || cp->k < 1 || cp->k > 6 || cp->term != PD_TERM_NONE) {
+        set_err(g->ctx, "pd_decimate_wup: density cost with k in [1, 6] only%s (k = %lld)", "",
+                cp ? cp->k : -1);
+        return PD_EINVAL;
+    }
+    if (m < 0 || m > g->n || !keep_dev) {
+        set_err(g->ctx, "pd_decimate_wup: m must be in [0, n] and keep_dev set%s (m = %lld)", "",
+                m);
+        return PD_EINVAL;
+    }
+    if (g->ng != g->n) {
+        set_err(g->ctx, "pd_decimate_wup: grid already decimated; build a new one%s", "", 0);
+        return PD_EINVAL;
+    }
+    memset(&g->stats, 0, sizeof(g->stats));
+    g->stats.leaf_max = g->T;
+    g->stats.n = g->n;
+    g->stats.m = m;
+    long long launches0 = g_launch_count;
+    RoundScratch rs(g);
+    Timers T(g->st);
+    cudaEventCreate(&rs.e0);
+    cudaEventCreate(&rs.e1);
+    cudaEventRecord(rs.e0, g->st);
+    // equal distances ordered by input index, so that the stored lists (and
+    // the adjacency of the removal rule) do not depend on the Morton order
+    pd_cost_params c2 = *cp;
+    c2.term = PD_TERM_INDEX_TIE;
+    int rc = prepare_state(g, &c2);
+    if (rc) return rc;
+    const int k = cp->k, S = g->S;
+    const int64_t cap = g->n;
+    uint8_t *wdirty, *pick;
+    u64* mark_p;
+    int* mark_i;
+    RALLOC(wdirty, uint8_t, cap);
+    RALLOC(pick, uint8_t, cap);
+    RALLOC(mark_p, u64, cap);
+    RALLOC(mark_i, int, cap);
+    SelBuffers sb;
+    RALLOC(sb.p[0], u64, cap);
+    RALLOC(sb.p[1], u64, cap);
+    RALLOC(sb.i[0], int, cap);
+    RALLOC(sb.i[1], int, cap);
+    RALLOC(sb.hist, uint32_t, 4096);
+    CK(cudaMemsetAsync(sb.hist, 0, 4096 * sizeof(uint32_t), g->st));
+    RoundDev* rd;
+    RALLOC(rd, RoundDev, 1);
+    int64_t live = g->n, built = g->n;
+    int iters = 0;
+    while (live > m) {
+        if (++iters > 100000) {
+            set_err(g->ctx, "pd_decimate_wup: iteration limit reached%s (live = %lld)", "", live);
+            return PD_EINTERNAL;
+        }
+        if (live * 2 < built) {
+            Span t(T, &g->stats.ms_build);
+            rc = compact_rebuild(g, false);
+            if (rc) return rc;
+            built = live;
+        }
+        // 1. every live point's S nearest and cost
+        {
+            Span t(T, &g->stats.ms_knn);
+            KnnArgs a = base_args(g, &c2);
+            a.qflag = g->alive;
+            CK(launch_knn(view_of(g), a, g->st));
+        }
+        CK(cudaMemsetAsync(wdirty, 0, g->ng, g->st));
+        // 2. w_up: the (live - m)-th largest key is the smallest one above it
+        RoundDev h;
+        memset(&h, 0, sizeof(h));
+        h.live = live;
+        h.m = m;
+        CK(cudaMemcpyAsync(rd, &h, sizeof(h), cudaMemcpyHostToDevice, g->st));
+        CK(wup_launch_setup(rd, g->st));
+        {
+            Span t(T, &g->stats.ms_select);
+            CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+        }
+        // 3. removal rounds above w_up
+        for (int r = 0;; r++) {
+            CK(wup_launch_round(bufview(g, &c2), g->alive, wdirty, g->ng, S, k, rd, mark_p,
+                                mark_i, pick, g->st));
+            unsigned long long removed = 0;
+            CK(cudaMemcpyAsync(&removed, &rd->removed, sizeof(removed), cudaMemcpyDeviceToHost,
+                               g->st));
+            CK(cudaStreamSynchronize(g->st));
+            g->stats.rounds++;
+            if ((int64_t)removed > live - m || (r == 0 && removed == 0)) {
+                set_err(g->ctx, "pd_decimate_wup: a round removed %s%lld points", "",
+                        (long long)removed);
+                return PD_EINTERNAL;
+            }
+            live -= (int64_t)removed;
+            if (g->trace)
+                fprintf(stderr, "pd wup iteration %d round %d removed %llu live %lld\n", iters, r,
+                        removed, (long long)live);
+            if (removed == 0 || live <= m) break;
+        }
+    }
+    g->stats.iterations = iters;
+    CK(cudaMemsetAsync(keep_dev, 0, g->n, g->st));
+    CK(launch_keep(g->pos, g->alive, g->ng, keep_dev, g->st));
+    cudaEventRecord(rs.e1, g->st);
+    CK(cudaEventSynchronize(rs.e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, rs.e0, rs.e1);
+    g->stats.ms_total = ms;
+    T.resolve();
+    g->stats.ms_rules = ms - g->stats.ms_knn - g->stats.ms_build;
+    g->stats.launches = g_launch_count - launches0;
+    g->ng = 0;  // consumed
+    return PD_OK;
+}
+
 extern "C" int pd_knn_cost(pd_grid* g, const pd_cost_params* cp, double* cost_dev,
                            int32_t* knn_dev, void* stream) {
     if (!g) return PD_EINVAL;
@@ -1035,6 +1165,19 @@ extern "C" int pd_decimate_count(pd_grid* g, const pd_cost_params* cp, int64_t m
     cudaError_t e = cudaStreamSynchronize(g->st);
     if (!rc && e) {
         set_err(g->ctx, "pd_decimate: CUDA error %s%lld", "", (long long)e);
+        rc = PD_ECUDA;
+    }
+    return rc;
+}
+
+extern "C" int pd_decimate_wup(pd_grid* g, const pd_cost_params* cp, int64_t m,
+                               uint8_t* keep_dev, void* stream) {
+    if (!g) return PD_EINVAL;
+    g->st = (cudaStream_t)stream;
+    int rc = wup_impl(g, cp, m, keep_dev);
+    cudaError_t e = cudaStreamSynchronize(g->st);
+    if (!rc && e) {
+        set_err(g->ctx, "pd_decimate_wup: CUDA error %s%lld", "", (long long)e);
         rc = PD_ECUDA;
     }
     return rc;

@@ -370,17 +370,20 @@ __device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& 
     for (int i = 0; i < S; i++) found += top.has(i);
     if (FILT == FILT_NONE) {
         if (a.density_k1) {
+            // all S nearest are stored (the k+b buffer); the shell is the
+            // prefix at the nearest distance d0, its size kept in flg >> 2
             u64 d0 = top.dist(0);
             int shell = 0;
 #pragma unroll
             for (int i = 0; i < S; i++) {
-                bool in = d0 != ~0ull && top.dist(i) == d0;
-                shell += in;
-                a.nbr[(int64_t)q * S + i] = in ? top.ident(i) : -1;
+                bool h = top.has(i);
+                shell += (h && top.dist(i) == d0) ? 1 : 0;
+                a.nbr[(int64_t)q * S + i] = h ? top.ident(i) : -1;
             }
             a.prim_out[q] = key_prim_d2(d0);
             a.rk2_out[q] = d0;
-            a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0));
+            a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0) | (shell << 2));
+            if (a.hz_out) a.hz_out[q] = top.has(S - 1) ? top.dist(S - 1) : ~0ull;
             if (a.cost_out) a.cost_out[q] = d0 == ~0ull ? 0.0 : __ddiv_rn(1.0, (double)d0);
         } else {
             int k = a.k;
@@ -506,10 +509,10 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
         }
     }
     // exactness bound: the R-th smallest distance must be exact
-    // k = 1 density: the nearest distance and its complete shell; other full
-    // searches: all S stored neighbours exact (the k+b neighbour buffer, so a
-    // removal can be absorbed without a new search); filtered searches: k.
-    const int R = FILT == FILT_NONE ? (a.density_k1 ? 1 : S) : a.k;
+    // full searches: all S stored neighbours exact (the k+b neighbour buffer,
+    // so a removal can be absorbed without a new search; for the k = 1
+    // density cost the nearest shell is then complete); filtered searches: k.
+    const int R = FILT == FILT_NONE ? S : a.k;
     bool todo = q >= 0;
     unsigned long long wpairs = 0;
     if (FILT == FILT_BELOW_TAU && a.hz_out) {

@@ -182,6 +182,11 @@ struct BufView {  // the k+b neighbour buffer of every point
     int term;
     double weight;
 };
+// k = 1 density cost: absorb removals in the stored nearest entries (the
+// shell at the new nearest distance must lie below the search horizon);
+// dirty[s] = 1 where a new search is needed.
+cudaError_t round_launch_k1_update(const BufView& b, const uint8_t* alive, int64_t n, int S,
+                                   uint8_t* dirty, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_kk_update(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
                                    uint8_t* dirty, RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_kk_cand2(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
@@ -224,4 +229,13 @@ cudaError_t launch_sample_rows(const int* pool, int64_t npool, u64 seed, long lo
                                int* rows, cudaStream_t st);
 cudaError_t launch_normal_fallback(const float* mlp, const float* onorm, const float* pca,
                                    int64_t n, float min_norm, float* out, cudaStream_t st);
+// ---------------------------------------------------------------- wup.cu
+// The paper's iterative w_up scheme: set the rank (live - m) for the key
+// selection of w_up, then run one removal round (marks, picks, removal,
+// stored-list update).  S <= 8, k <= S.
+cudaError_t wup_launch_setup(RoundDev* rd, cudaStream_t st);
+cudaError_t wup_launch_round(const BufView& b, uint8_t* alive, uint8_t* wdirty, int64_t n, int S,
+                             int k, RoundDev* rd, u64* mark_p, int* mark_i, uint8_t* pick,
+                             cudaStream_t st);
+
 }  // namespace pd

@@ -134,16 +134,19 @@ __global__ void sel_compact_kernel(const u64* __restrict__ prim, const int4* __r
     }
 }
 
-// (B) for k = 1: a shell member of larger input index must be in P.
+// (B) for k = 1: a shell member of larger input index must be in P.  The
+// shell is the first flg >> 2 stored neighbours.
 __global__ void k1_fix_kernel(const int* __restrict__ cand, const int* __restrict__ ncand,
-                              const int4* __restrict__ pos, const int* __restrict__ nbr, int S,
+                              const int4* __restrict__ pos, const int* __restrict__ nbr,
+                              const uint8_t* __restrict__ flg, int S,
                               const uint8_t* __restrict__ inP, uint8_t* rej, int* changed) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *ncand) return;
     int s = cand[t];
     if (rej[s]) return;
     int is = pos[s].w;
-    for (int i = 0; i < S; i++) {
+    int shell = flg[s] >> 2;
+    for (int i = 0; i < shell; i++) {
         int x = nbr[(int64_t)s * S + i];
         if (x < 0) continue;
         if (pos[x].w > is && (!inP[x] || rej[x])) {
@@ -574,10 +577,10 @@ cudaError_t launch_sel_compact(const u64* prim, const int4* pos, const uint8_t* 
     return cudaGetLastError();
 }
 cudaError_t launch_k1_fix(const int* cand, const int* ncand, int max_cand, const int4* pos,
-                          const int* nbr, int S, const uint8_t* inP, uint8_t* rej, int* changed,
-                          cudaStream_t st) {
+                          const int* nbr, const uint8_t* flg, int S, const uint8_t* inP,
+                          uint8_t* rej, int* changed, cudaStream_t st) {
     if (max_cand <= 0) return cudaSuccess;
-    k1_fix_kernel<<<GRID1(max_cand), 0, st>>>(cand, ncand, pos, nbr, S, inP, rej, changed); note_launch();
+    k1_fix_kernel<<<GRID1(max_cand), 0, st>>>(cand, ncand, pos, nbr, flg, S, inP, rej, changed); note_launch();
     return cudaGetLastError();
 }
 cudaError_t round_launch_danger(const GridView& g, const int* src, const u64* prim,

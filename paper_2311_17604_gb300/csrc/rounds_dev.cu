@@ -203,14 +203,17 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
     u64 ps = prim[s];
     int is = pos[s].w;
     if (key_gt(rd->tau_prim, rd->tau_idx, ps, is)) return;
-    if (flg[s] & 2) {
+    uint8_t fl = flg[s];
+    if (fl & 2) {
         slow[atomicAdd(&rd->nslow, 1)] = (int)s;
         return;
     }
-    bool ok = nbr[s * S] < 0;
-    for (int i = 0; i < S && !ok; i++) {
+    // the shell (points at the nearest distance) is the first fl >> 2 stored
+    // neighbours; none: a lone point
+    int shell = fl >> 2;
+    bool ok = shell == 0;
+    for (int i = 0; i < shell && !ok; i++) {
         int x = nbr[s * S + i];
-        if (x < 0) continue;
         if (key_gt(ps, is, prim[x], pos[x].w)) ok = true;
     }
     if (ok) {
@@ -276,17 +279,18 @@ __global__ void k1d_slow_kernel(GridView g, const u64* __restrict__ prim,
 }
 
 __global__ void k1d_fix_kernel(const int* __restrict__ cand, const int4* __restrict__ pos,
-                               const int* __restrict__ nbr, int S, const uint8_t* __restrict__ inP,
-                               uint8_t* rej, int iter, RoundDev* rd) {
+                               const int* __restrict__ nbr, const uint8_t* __restrict__ flg, int S,
+                               const uint8_t* __restrict__ inP, uint8_t* rej, int iter,
+                               RoundDev* rd) {
     if (iter > 0 && !rd->changed[iter - 1]) return;
     int nc = rd->ncand;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
         int s = cand[t];
         if (rej[s]) continue;
         int is = pos[s].w;
-        for (int i = 0; i < S; i++) {
+        int shell = flg[s] >> 2;
+        for (int i = 0; i < shell; i++) {
             int x = nbr[(int64_t)s * S + i];
-            if (x < 0) continue;
             if (pos[x].w > is && (!inP[x] || rej[x])) {
                 rej[s] = 1;
                 rd->changed[iter] = 1;
@@ -364,6 +368,72 @@ __global__ void dirtyd_kernel(const uint8_t* __restrict__ alive, const int* __re
     }
     unsigned c = __popc(__ballot_sync(FULLM, d));
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->tot_requery, (unsigned long long)c);
+}
+
+// ------------------------------------------------------------------ k = 1 buffer
+// k = 1 density cost: every point stores its S nearest live points exactly,
+// with the horizon h = the S-th squared distance at search time (any live
+// point not stored lies at d^2 >= h; h = ~0 when all live points were
+// stored).  After removals, the first live stored entry is the new nearest;
+// its shell (the stored entries at that distance) is complete when that
+// distance is below h, and the key follows without a search.  Otherwise, or
+// when no stored entry is left, the point is searched again.
+#define K1_SMAX 8
+
+__global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
+                                  uint8_t* dirty, RoundDev* rd) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool upd = false, req = false;
+    if (s < n) {
+        uint8_t dv = 0;
+        if (alive[s]) {
+            int ids[K1_SMAX];
+            int r = 0;
+            bool dead = false;
+#pragma unroll
+            for (int i = 0; i < K1_SMAX; i++) {
+                ids[i] = -1;
+                if (i < S) {
+                    int x = b.nbr[s * S + i];
+                    if (x >= 0) {
+                        if (alive[x]) ids[r++] = x;
+                        else dead = true;
+                    }
+                }
+            }
+            if (dead) {
+                u64 h = b.hz[s];
+                u64 d0 = ~0ull;
+                int shell = 0;
+                if (r > 0) {
+                    int4 ps = b.pos[s];
+                    d0 = sqd(ps, b.pos[ids[0]]);
+                    shell = 1;
+#pragma unroll
+                    for (int i = 1; i < K1_SMAX; i++)
+                        if (i < r && sqd(ps, b.pos[ids[i]]) == d0) shell++;
+                }
+                if (r > 0 && (h == ~0ull || d0 < h)) {
+                    b.prim[s] = key_prim_d2(d0);
+                    b.rk2[s] = d0;
+                    b.flg[s] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell << 2));
+#pragma unroll
+                    for (int i = 0; i < K1_SMAX; i++)
+                        if (i < S) b.nbr[s * S + i] = ids[i];
+                    upd = true;
+                } else {
+                    dv = 1;
+                    req = true;
+                }
+            }
+        }
+        dirty[s] = dv;
+    }
+    unsigned cu = __popc(__ballot_sync(FULLM, upd)), cr = __popc(__ballot_sync(FULLM, req));
+    if ((threadIdx.x & 31) == 0) {
+        if (cu) atomicAdd(&rd->tot_updated, (unsigned long long)cu);
+        if (cr) atomicAdd(&rd->tot_requery, (unsigned long long)cr);
+    }
 }
 
 // ------------------------------------------------------------------ k+b buffer
@@ -557,7 +627,7 @@ cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* a
     k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, flg, n, S, rd, inP, cand, slow); note_launch();
     k1d_slow_kernel<<<PERSIST_BLOCKS, 128, 0, st>>>(g, prim, alive, rk2, slow, rd, inP, cand); note_launch();
     for (int it = 0; it < PD_FIX_ITERS; it++) {
-        k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, g.pos, nbr, S, inP, rej, it, rd); note_launch();
+        k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, g.pos, nbr, flg, S, inP, rej, it, rd); note_launch();
     }
     return cudaGetLastError();
 }
@@ -592,6 +662,12 @@ cudaError_t round_launch_dirty(const uint8_t* alive, const int* nbr, int64_t n, 
 }  // namespace pd
 
 namespace pd {
+cudaError_t round_launch_k1_update(const BufView& b, const uint8_t* alive, int64_t n, int S,
+                                   uint8_t* dirty, RoundDev* rd, cudaStream_t st) {
+    if (S > K1_SMAX) return cudaErrorInvalidValue;
+    k1d_update_kernel<<<GRID1(n), 0, st>>>(b, alive, n, S, dirty, rd); note_launch();
+    return cudaGetLastError();
+}
 cudaError_t round_launch_kk_update(const BufView& b, const uint8_t* alive, int64_t n, int S, int k,
                                    uint8_t* dirty, RoundDev* rd, cudaStream_t st) {
     kkd_update_kernel<<<GRID1(n), 0, st>>>(b, alive, n, S, k, dirty, rd); note_launch();

@@ -24,7 +24,7 @@ PD_STATIC_MAX_POINTS = 65536
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
             "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch",
-            "pd_autotune",
+            "pd_autotune", "pd_decimate_wup",
             # pd_normals.h
             "pd_normals_pca", "pd_mlp_init", "pd_mlp_forward", "pd_mlp_grad", "pd_mlp_train",
             "pd_normals_mlp",
@@ -73,7 +73,7 @@ class pd_stats(ctypes.Structure):
                 ("ms_knn_requery", ctypes.c_double), ("ms_rules", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("ms_select", ctypes.c_double),
                 ("ms_danger", ctypes.c_double), ("pairs_first", ctypes.c_int64),
-                ("leaf_max", ctypes.c_int32), ("reserved_stats", ctypes.c_int32)]
+                ("leaf_max", ctypes.c_int32), ("iterations", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -154,6 +154,7 @@ def lib():
         L.pd_knn_cost.argtypes = [P, ctypes.POINTER(pd_cost_params), P, P, P]
         L.pd_decimate_count.argtypes = [P, ctypes.POINTER(pd_cost_params), I64, P, P]
         L.pd_decimate_ratio.argtypes = [P, ctypes.POINTER(pd_cost_params), ctypes.c_double, P, P]
+        L.pd_decimate_wup.argtypes = [P, ctypes.POINTER(pd_cost_params), I64, P, P]
         L.pd_grid_stats.argtypes = [P, ctypes.POINTER(pd_stats)]
         L.pd_decimate_host.argtypes = [P, P, P, P, I64, ctypes.POINTER(pd_cost_params), I64, P,
                                        P, ctypes.POINTER(pd_stats)]
@@ -331,6 +332,18 @@ def pd_decimate_count(grid: Grid, m, k=1, term=PD_TERM_NONE, weight=0.0, normals
     rc = lib().pd_decimate_count(grid.h, ctypes.byref(cp), int(m), _ptr(keep),
                                  _stream_ptr(stream))
     grid.ctx.check(rc, "pd_decimate_count")
+    return keep
+
+
+def pd_decimate_wup(grid: Grid, m, k=1, keep=None, stream=None):
+    """The paper's iterative w_up scheme (parallel removal rounds); returns
+    the uint8 keep mask [n] (exactly m ones)."""
+    torch = _torch()
+    if keep is None:
+        keep = torch.empty(grid.n, dtype=torch.uint8, device="cuda")
+    cp = cost_params(k)
+    rc = lib().pd_decimate_wup(grid.h, ctypes.byref(cp), int(m), _ptr(keep), _stream_ptr(stream))
+    grid.ctx.check(rc, "pd_decimate_wup")
     return keep
 
 
