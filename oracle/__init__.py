@@ -61,6 +61,9 @@ def _load():
             lib.orc_knn_query.restype = ctypes.c_int
             lib.orc_radius_counts.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, P]
             lib.orc_radius_counts.restype = ctypes.c_int
+            lib.orc_decimate_wup.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int64, ctypes.c_int, P, P, P]
+            lib.orc_decimate_wup.restype = ctypes.c_int
             lib.orc_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -157,6 +160,32 @@ def decimate(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None, backend=KDTRE
     if want_order:
         return keep, order, pkey
     return keep
+
+
+def wup_width(k: int) -> int:
+    """Stored neighbours of the w_up mode for k (the k+b buffer): 8 for k <= 6."""
+    if not 1 <= k <= 6:
+        raise ValueError("the w_up mode supports k in [1, 6]")
+    return 8
+
+
+def decimate_wup(xyz, k, m, S=None, backend=KDTREE):
+    """The paper's iterative w_up scheme (section "Sub-sampling algorithm")
+    with each sweep restated as parallel rounds of non-interacting removals.
+
+    Returns (keep uint8 [n], iterations, rounds).
+    """
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+    n = xyz.shape[0]
+    S = wup_width(k) if S is None else S
+    keep = np.empty(n, dtype=np.uint8)
+    it = ctypes.c_int32(0)
+    rd = ctypes.c_int64(0)
+    rc = _load().orc_decimate_wup(_ptr(xyz), n, k, S, m, backend, _ptr(keep), ctypes.byref(it),
+                                  ctypes.byref(rd))
+    if rc != 0:
+        raise ValueError("orc_decimate_wup: invalid arguments")
+    return keep, int(it.value), int(rd.value)
 
 
 def target_count(n: int, ratio: float) -> int:

@@ -625,6 +625,169 @@ int orc_radius_counts(const int32_t* xyz, int64_t n, const int64_t* r2, int nr,
     return 0;
 }
 
+/*
+ * The paper's iterative scheme (section "Sub-sampling algorithm"), with its
+ * sweep restated as parallel rounds so that a GPU can run it and reproduce it
+ * exactly.  Density cost (Eq. 10/11), k nearest, a buffer of S >= k stored
+ * neighbours (the k+b extended neighbourhood).  Until m points remain:
+ *
+ *   1. Cost updates: the S nearest live points, in (d^2, index) order, and
+ *      the cost of every live point are recomputed exactly; no point is
+ *      dirty.
+ *   2. w_up = the m-th smallest key (cost, index) among the live points:
+ *      the points above it are the live - m largest keys.
+ *   3. Point removal, in rounds until no clean live point lies above w_up:
+ *      a candidate is a clean live point whose key is above w_up; a
+ *      candidate is removed when no other candidate adjacent to it has a
+ *      larger key, adjacency meaning that one of the two lies among the k
+ *      first stored neighbours of the other.  Every live point that stored
+ *      a removed point drops it; with at least k stored points left its
+ *      cost is recomputed from the first k of them (the stored points are
+ *      the nearest live points, ties aside, so that cost is exact), with
+ *      fewer it is flagged dirty and is not removed before the next
+ *      iteration's cost update.
+ *
+ * The paper sweeps its voxels in order, removing every point above w_up
+ * and updating its reverse neighbours as it goes; here all non-interacting
+ * removals of a sweep happen at once, the largest key first among
+ * interacting ones.  Removals never raise a cost, so at most live - m
+ * points leave per iteration (never fewer than m remain) and at least one
+ * leaves (the largest key is never blocked).
+ *   keep_out    n bytes.  iters_out, rounds_out: may be NULL.
+ * Returns 0, or -1 on invalid arguments (k in [1, S], S <= ORC_KMAX).
+ */
+static inline int keygt(double ca, int32_t ia, double cb, int32_t ib) {
+    return ca > cb || (ca == cb && ia > ib);
+}
+
+typedef struct {
+    double c;
+    int32_t i;
+} ckey;
+
+/* descending key order */
+static int ckey_cmp(const void* a, const void* b) {
+    const ckey* x = (const ckey*)a;
+    const ckey* y = (const ckey*)b;
+    if (keygt(x->c, x->i, y->c, y->i)) return -1;
+    if (keygt(y->c, y->i, x->c, x->i)) return 1;
+    return 0;
+}
+
+int orc_decimate_wup(const int32_t* xyz, int64_t n, int k, int S, int64_t m, int backend,
+                     uint8_t* keep_out, int32_t* iters_out, int64_t* rounds_out) {
+    if (!xyz || n < 0 || n > INT32_MAX || k < 1 || S < k || S > ORC_KMAX || !keep_out ||
+        m < 0 || m > n)
+        return -1;
+    const int64_t N = n > 0 ? n : 1;
+    uint8_t* live = (uint8_t*)malloc((size_t)N);
+    uint8_t* dirty = (uint8_t*)malloc((size_t)N);
+    uint8_t* cand = (uint8_t*)malloc((size_t)N);
+    uint8_t* pick = (uint8_t*)malloc((size_t)N);
+    int64_t* nd2 = (int64_t*)malloc((size_t)N * S * sizeof(int64_t));
+    int32_t* nid = (int32_t*)malloc((size_t)N * S * sizeof(int32_t));
+    int32_t* ncnt = (int32_t*)malloc((size_t)N * sizeof(int32_t));
+    double* cost = (double*)malloc((size_t)N * sizeof(double));
+    double* bc = (double*)malloc((size_t)N * sizeof(double));  /* largest adjacent key: cost */
+    int32_t* bi = (int32_t*)malloc((size_t)N * sizeof(int32_t)); /* ... and index */
+    ckey* order = (ckey*)malloc((size_t)N * sizeof(ckey));
+    memset(live, 1, (size_t)n);
+    int64_t nlive = n, rounds = 0;
+    int32_t iters = 0;
+    cost_cfg cc = {k, ORC_TERM_NONE, 0.0, NULL, NULL};
+    while (nlive > m) {
+        iters++;
+        /* 1. exact S nearest and cost of every live point */
+        searcher sr;
+        searcher_init(&sr, xyz, n, backend, live);
+#pragma omp parallel for schedule(dynamic, 1024)
+        for (int64_t q = 0; q < n; q++) {
+            if (!live[q]) continue;
+            ncnt[q] = searcher_knn(&sr, live, q, S, nd2 + q * S, nid + q * S);
+            cost[q] = cost_of(&cc, q, nd2 + q * S, nid + q * S, ncnt[q] < k ? ncnt[q] : k);
+            dirty[q] = 0;
+        }
+        searcher_free(&sr);
+        /* 2. w_up: the (nlive - m)-th largest key is the smallest one above it */
+        int64_t nl = 0;
+        for (int64_t q = 0; q < n; q++)
+            if (live[q]) {
+                order[nl].c = cost[q];
+                order[nl].i = (int32_t)q;
+                nl++;
+            }
+        qsort(order, (size_t)nl, sizeof(ckey), ckey_cmp);
+        const double tc = order[nlive - m - 1].c;
+        const int32_t ti = order[nlive - m - 1].i;
+        /* 3. rounds of removals above w_up */
+        for (;;) {
+            int64_t nc = 0;
+            for (int64_t q = 0; q < n; q++) {
+                cand[q] = live[q] && !dirty[q] && !keygt(tc, ti, cost[q], (int32_t)q);
+                nc += cand[q];
+                bc[q] = -1.0;
+                bi[q] = -1;
+            }
+            if (!nc) break;
+            /* the largest candidate key that stores each point among its first k */
+            for (int64_t q = 0; q < n; q++) {
+                if (!cand[q]) continue;
+                int lim = ncnt[q] < k ? ncnt[q] : k;
+                for (int i = 0; i < lim; i++) {
+                    int32_t x = nid[q * S + i];
+                    if (keygt(cost[q], (int32_t)q, bc[x], bi[x])) {
+                        bc[x] = cost[q];
+                        bi[x] = (int32_t)q;
+                    }
+                }
+            }
+            int64_t np = 0;
+            for (int64_t q = 0; q < n; q++) {
+                pick[q] = 0;
+                if (!cand[q]) continue;
+                if (keygt(bc[q], bi[q], cost[q], (int32_t)q)) continue;
+                int ok = 1, lim = ncnt[q] < k ? ncnt[q] : k;
+                for (int i = 0; i < lim && ok; i++) {
+                    int32_t x = nid[q * S + i];
+                    if (cand[x] && keygt(cost[x], x, cost[q], (int32_t)q)) ok = 0;
+                }
+                pick[q] = (uint8_t)ok;
+                np += ok;
+            }
+            rounds++;
+            for (int64_t q = 0; q < n; q++)
+                if (pick[q]) live[q] = 0;
+            nlive -= np;
+            /* drop removed points from the stored lists */
+            for (int64_t q = 0; q < n; q++) {
+                if (!live[q]) continue;
+                int r = 0, dead = 0;
+                for (int i = 0; i < ncnt[q]; i++) {
+                    int32_t x = nid[q * S + i];
+                    if (live[x]) {
+                        nid[q * S + r] = x;
+                        nd2[q * S + r] = nd2[q * S + i];
+                        r++;
+                    } else {
+                        dead = 1;
+                    }
+                }
+                if (!dead) continue;
+                ncnt[q] = r;
+                if (r >= k) cost[q] = cost_of(&cc, q, nd2 + q * S, nid + q * S, k);
+                else dirty[q] = 1;
+            }
+            if (nlive <= m) break;
+        }
+    }
+    for (int64_t q = 0; q < n; q++) keep_out[q] = live[q];
+    if (iters_out) *iters_out = iters;
+    if (rounds_out) *rounds_out = rounds;
+    free(live); free(dirty); free(cand); free(pick); free(nd2); free(nid); free(ncnt);
+    free(cost); free(bc); free(bi); free(order);
+    return 0;
+}
+
 int orc_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -134,3 +134,61 @@ def best_spacing2(xyz, m):
         sel[list(sub)] = True
         best = max(best, min_spacing2(xyz, sel))
     return best
+
+
+def wup_from_scratch(xyz, k, m, S):
+    """The iterative w_up scheme with parallel removal rounds, written out
+    plainly (pure Python lists, brute-force neighbours) as a second check of
+    the C oracle's orc_decimate_wup.  Returns (keep, iterations)."""
+    x = [tuple(int(v) for v in p) for p in np.asarray(xyz)]
+    n = len(x)
+    live = [True] * n
+
+    def d2(a, b):
+        return sum((x[a][t] - x[b][t]) ** 2 for t in range(3))
+
+    def cost_of(p, lst):
+        c = 0.0
+        for q in lst[:k]:
+            dd = d2(p, q)
+            c = c + (1.0 / dd if dd else math.inf)
+        return c
+
+    iters = 0
+    while sum(live) > m:
+        iters += 1
+        nbr, key, dirty = {}, {}, set()
+        for p in range(n):
+            if live[p]:
+                others = sorted((d2(p, q), q) for q in range(n) if q != p and live[q])
+                nbr[p] = [q for _, q in others[:S]]
+                key[p] = (cost_of(p, nbr[p]), p)
+        order = sorted((key[p] for p in key), reverse=True)
+        tau = order[sum(live) - m - 1]
+        while True:
+            cand = {p for p in key if live[p] and p not in dirty and key[p] >= tau}
+            if not cand:
+                break
+            blocked = set()
+            for q in cand:
+                for x_ in nbr[q][:k]:
+                    if key[q] > key[x_]:
+                        blocked.add(x_)
+                    elif x_ in cand and key[x_] > key[q]:
+                        blocked.add(q)
+            picks = cand - blocked
+            for p in picks:
+                live[p] = False
+            for p in list(key):
+                if not live[p]:
+                    continue
+                kept = [q for q in nbr[p] if live[q]]
+                if len(kept) != len(nbr[p]):
+                    nbr[p] = kept
+                    if len(kept) >= k:
+                        key[p] = (cost_of(p, kept), p)
+                    else:
+                        dirty.add(p)
+            if sum(live) <= m:
+                break
+    return np.array(live, dtype=np.uint8), iters
