@@ -189,15 +189,27 @@ def run_reference(args, wl, rank):
 
 
 
-# ------------------------------------------------------------------ roofline of the kNN pass
-# DRAM bytes per query of knn_kernel<8,0> (the first full pass), from one
-# `ncu --set full` capture of `bench.py --knn-only` on the outdoor scan, valid
-# while the kernel's sources hash to KNN_SRC_SHA (else traffic is reported null).
-KNN_SRC_SHA = "1d194461d3f93c2c"
-KNN_DRAM_BYTES_PER_QUERY = 111.7   # 525.3 MB read + 634.4 MB written / 10,385,229 queries
+# ------------------------------------------------------------------ rooflines
+# Algorithmic (compulsory) HBM bytes of the hot path per unit of work, as the
+# measurement plan counts them:
+#   kNN/cost (A4), per query: 12 B read (x, y, z), 12 B key + index, 8 B r_k^2
+#                  and 4 k B neighbour indices written: 36 B (k = 1), 48 B (k = 4)
+#   removal rounds (A5-A6): 16 B per live point per round
+#   grid build (A1-A3), per point: 24 B cell key, 24 B per radix pass, 28 B gather
+def knn_bytes(k):
+    return 12 + 12 + 8 + 4 * k
+
+
+ROUND_BYTES_PER_LIVE = 16
+ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop: exact int distance test
+
+# DRAM bytes per query of the first full kNN pass (knn_kernel<8,0,0,0>), from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a one-station
+# site scan at the leaf capacity below; reported only while the kNN sources
+# hash to src_sha and the timed run uses the same leaf capacity and k.
+KNN_TRAFFIC = {"k": 1, "leaf_max": 0, "bytes_per_query": None, "src_sha": ""}
 KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
                "paper_2311_17604_gb300/csrc/pd_kernels.h"]
-ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop: exact int distance test
 
 
 def knn_src_sha():
@@ -209,35 +221,64 @@ def knn_src_sha():
     return h.hexdigest()[:16]
 
 
-def knn_roofline(stats, k, clk, device):
-    """The first full kNN/cost pass (one launch per step).  It is bound by
-    integer issue, not HBM: achieved = candidate pairs scanned x 9 integer ops
-    / launch time, against the issue peak SMs x 4 schedulers x 32 lanes x SM
-    clock.  The HBM view (algorithmic bytes / time / measured copy bandwidth)
-    is reported beside it."""
+def radix_passes(xyz):
+    """Radix passes of the grid build: 8-bit digits over 3 B Morton bits."""
+    span = int((xyz.max(axis=0).astype(np.int64) - xyz.min(axis=0)).max())
+    B = max(1, min(span.bit_length(), 21))
+    return (3 * B + 7) // 8
+
+
+def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
+    """HBM rooflines from the library's CUDA-event phase timers (on the
+    launching stream) and the algorithmic bytes above.  The dominant kernel of
+    a step is the kNN/cost search (its first full pass plus the re-searches of
+    the removal rounds); the first pass alone, its integer-issue view, the
+    other phases and the whole step are reported beside it."""
     import torch
-    S = 8 if k <= 6 else 17
-    # read {x,y,z,i}; write key, r_k^2, flags, S neighbours and (k >= 2) the horizon
-    per_q = 16 + 8 + 8 + 1 + 4 * S + (8 if k >= 2 else 0)
-    ms = statistics.mean(s["ms_knn_first"] for s in stats)
-    q = statistics.mean(s["q_first"] for s in stats)
-    pairs = statistics.mean(s["pairs_first"] for s in stats)
+    mean = lambda key: statistics.mean(s[key] for s in stats)
+    peak, kind = measured_peaks()
+    bq = knn_bytes(k)
+    q1, ms1 = mean("q_first"), mean("ms_knn_first")
+    rq, msr = mean("requeries"), mean("ms_knn_requery")
+    pairs = mean("pairs_first")
+    ms_knn = ms1 + msr
+    gbs = lambda b, ms: b / (ms / 1e3) / 1e9 if ms > 0 else None
+    knn_ach = gbs((q1 + rq) * bq, ms_knn)
+    sha = knn_src_sha()
+    tr = KNN_TRAFFIC
+    traffic = (tr["bytes_per_query"] * (q1 + rq)
+               if tr["bytes_per_query"] and tr["src_sha"] == sha and tr["leaf_max"] == leaf
+               and tr["k"] == k else None)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     peak_ops = sms * 4 * 32 * mhz * 1e6
-    achieved = pairs * ALU_OPS_PER_PAIR / (ms / 1e3)
-    hbm_peak, hbm_kind = measured_peaks()
-    hbm = q * per_q / (ms / 1e3) / 1e9
-    sha = knn_src_sha()
-    traffic = (KNN_DRAM_BYTES_PER_QUERY * q) if sha == KNN_SRC_SHA and KNN_DRAM_BYTES_PER_QUERY else None
-    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-            "frac": achieved / peak_ops, "traffic": traffic,
-            "kernel": "knn_kernel<%d,0> (first full pass)" % S, "ms": ms, "queries": q,
-            "pairs_per_query": pairs / max(q, 1), "ops_per_pair": ALU_OPS_PER_PAIR,
-            "peak_basis": "%d SMs x 4 x 32 lanes x %.0f MHz (median SM clock sampled)" % (sms, mhz),
-            "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
-                    "bytes_per_query": per_q, "peak_kind": hbm_kind},
-            "src_sha": sha}
+    alu = pairs * ALU_OPS_PER_PAIR / (ms1 / 1e3)
+    build_b = n * (24 + 24 * passes + 28)
+    round_b = mean("live_rounds") * ROUND_BYTES_PER_LIVE
+    step_b = build_b + (q1 + rq) * bq + round_b
+    step_ach = gbs(step_b, statistics.mean(step_ms))
+    phases = {"grid": mean("ms_grid"), "rebuilds": mean("ms_build"), "knn_first": ms1,
+              "knn_requery": msr, "select": mean("ms_select"),
+              "rules_other": mean("ms_rules") - mean("ms_select"),
+              "total": mean("ms_total")}
+    return {"bound": "hbm", "kernel": "knn_kernel: kNN/cost search (first full pass + re-searches)",
+            "achieved": knn_ach, "peak": peak, "unit": "GB/s", "frac": knn_ach / peak,
+            "peak_kind": kind, "traffic": traffic,
+            "units": q1 + rq, "unit_name": "queries", "bytes_per_unit": bq, "ms": ms_knn,
+            "first_pass": {"queries": q1, "ms": ms1, "achieved": gbs(q1 * bq, ms1),
+                           "frac": gbs(q1 * bq, ms1) / peak,
+                           "pairs_per_query": pairs / max(q1, 1),
+                           "alu": {"achieved": alu / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                                   "frac": alu / peak_ops, "ops_per_pair": ALU_OPS_PER_PAIR,
+                                   "peak_basis": "%d SMs x 4 x 32 lanes x %.0f MHz (median SM "
+                                                 "clock sampled)" % (sms, mhz)}},
+            "requeries": {"queries": rq, "ms": msr, "achieved": gbs(rq * bq, msr),
+                          "frac": (gbs(rq * bq, msr) or 0) / peak},
+            "step": {"bytes": step_b, "achieved": step_ach, "frac": step_ach / peak,
+                     "bytes_basis": "build %d B/pt (%d radix passes) + %d B per query + %d B "
+                                    "per live point per round" % (24 + 24 * passes + 28, passes,
+                                                                  bq, ROUND_BYTES_PER_LIVE)},
+            "phases_ms": phases, "src_sha": sha}
 
 # ------------------------------------------------------------------ batched and served legs
 def _pct(v, q):
@@ -506,7 +547,8 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
                "d2h_bytes_per_step": n}
 
-    roofline = knn_roofline(stats, k, clk, torch.cuda.current_device())
+    roofline = rooflines(stats, n, k, leaf, radix_passes(scan.xyz), step_ms, clk,
+                         torch.cuda.current_device())
     if rank != 0:
         return
     cpu = None

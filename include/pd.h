@@ -110,6 +110,8 @@ typedef struct {
     int64_t pairs_first;      /* (query, candidate) pairs the first pass scanned */
     int32_t leaf_max;         /* the grid's octree leaf capacity */
     int32_t iterations;       /* pd_decimate_wup: cost-update iterations (0 otherwise) */
+    double ms_grid;           /* device time of the pd_build_grid call that made the grid */
+    int64_t live_rounds;      /* sum over the removal rounds of the live count */
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */

@@ -62,7 +62,8 @@ def _load():
             lib.orc_radius_counts.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, P]
             lib.orc_radius_counts.restype = ctypes.c_int
             lib.orc_decimate_wup.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_int64, ctypes.c_int, P, P, P]
+                                             ctypes.c_int64, ctypes.c_int, P, P, P, P,
+                                             ctypes.c_int64]
             lib.orc_decimate_wup.restype = ctypes.c_int
             lib.orc_threads.restype = ctypes.c_int
             _lib = lib
@@ -169,11 +170,12 @@ def wup_width(k: int) -> int:
     return 8
 
 
-def decimate_wup(xyz, k, m, S=None, backend=KDTREE):
+def decimate_wup(xyz, k, m, S=None, backend=KDTREE, want_log=False):
     """The paper's iterative w_up scheme (section "Sub-sampling algorithm")
     with each sweep restated as parallel rounds of non-interacting removals.
 
-    Returns (keep uint8 [n], iterations, rounds).
+    Returns (keep uint8 [n], iterations, rounds); with ``want_log`` also the
+    list of (iteration, points removed) of every round.
     """
     xyz = np.ascontiguousarray(xyz, dtype=np.int32)
     n = xyz.shape[0]
@@ -181,10 +183,16 @@ def decimate_wup(xyz, k, m, S=None, backend=KDTREE):
     keep = np.empty(n, dtype=np.uint8)
     it = ctypes.c_int32(0)
     rd = ctypes.c_int64(0)
+    cap = 100000 if want_log else 0
+    log = np.zeros(max(cap, 1), dtype=np.int64)
     rc = _load().orc_decimate_wup(_ptr(xyz), n, k, S, m, backend, _ptr(keep), ctypes.byref(it),
-                                  ctypes.byref(rd))
+                                  ctypes.byref(rd), _ptr(log) if want_log else None, cap)
     if rc != 0:
         raise ValueError("orc_decimate_wup: invalid arguments")
+    if want_log:
+        nr = min(int(rd.value), cap)
+        return keep, int(it.value), int(rd.value), [(int(v >> 40), int(v & ((1 << 40) - 1)))
+                                                    for v in log[:nr]]
     return keep, int(it.value), int(rd.value)
 
 

@@ -654,6 +654,8 @@ int orc_radius_counts(const int32_t* xyz, int64_t n, const int64_t* r2, int nr,
  * points leave per iteration (never fewer than m remain) and at least one
  * leaves (the largest key is never blocked).
  *   keep_out    n bytes.  iters_out, rounds_out: may be NULL.
+ *   round_log   (may be NULL) per round: (iteration << 40) | points removed,
+ *               the first log_cap rounds.
  * Returns 0, or -1 on invalid arguments (k in [1, S], S <= ORC_KMAX).
  */
 static inline int keygt(double ca, int32_t ia, double cb, int32_t ib) {
@@ -675,7 +677,8 @@ static int ckey_cmp(const void* a, const void* b) {
 }
 
 int orc_decimate_wup(const int32_t* xyz, int64_t n, int k, int S, int64_t m, int backend,
-                     uint8_t* keep_out, int32_t* iters_out, int64_t* rounds_out) {
+                     uint8_t* keep_out, int32_t* iters_out, int64_t* rounds_out,
+                     int64_t* round_log, int64_t log_cap) {
     if (!xyz || n < 0 || n > INT32_MAX || k < 1 || S < k || S > ORC_KMAX || !keep_out ||
         m < 0 || m > n)
         return -1;
@@ -754,6 +757,7 @@ int orc_decimate_wup(const int32_t* xyz, int64_t n, int k, int S, int64_t m, int
                 pick[q] = (uint8_t)ok;
                 np += ok;
             }
+            if (round_log && rounds < log_cap) round_log[rounds] = ((int64_t)iters << 40) | np;
             rounds++;
             for (int64_t q = 0; q < n; q++)
                 if (pick[q]) live[q] = 0;

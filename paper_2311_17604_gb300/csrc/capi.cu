@@ -132,6 +132,7 @@ struct pd_grid {
     unsigned long long* d_u64;   // [0] counts
     std::vector<void*> owned;
     pd_stats stats;
+    double ms_grid;  // device time of the pd_build_grid call
     int trace;       // PD_TRACE set: one line per removal round on stderr
     int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
 };
@@ -194,6 +195,29 @@ GridView view_of(const pd_grid* g) {
     } while (0)
 
 void gfree(pd_grid* g, void* p) { ctx_free(g->ctx, p, g->st); }
+
+// Temporary device blocks of one function: released (stream-ordered) when the
+// function returns, on error paths too; done() releases one early.
+struct Temps {
+    pd_grid* g;
+    std::vector<void*> p;
+    explicit Temps(pd_grid* gg) : g(gg) {}
+    ~Temps() {
+        for (void* x : p) gfree(g, x);
+    }
+    void done(void* x) {
+        for (auto& y : p)
+            if (y == x) {
+                gfree(g, y);
+                y = nullptr;
+            }
+    }
+};
+#define TALLOC(t, ptr, type, count)           \
+    do {                                      \
+        ALLOC(ptr, type, count);              \
+        (t).p.push_back((void*)(ptr));        \
+    } while (0)
 
 // S = stored neighbours per point for a cost with k neighbours
 int width_for(int k, int density_k1) {
@@ -318,6 +342,10 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
         rc = (x);               \
         if (rc) return fail(rc); \
     } while (0)
+    cudaEvent_t be0 = nullptr, be1 = nullptr;
+    cudaEventCreate(&be0);
+    cudaEventCreate(&be1);
+    cudaEventRecord(be0, g->st);
     auto body = [&]() -> int {
         ALLOC(g->d_int, int, 8);
         ALLOC(g->d_u64, unsigned long long, 4);
@@ -341,22 +369,31 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
         if (g->B < 1) g->B = 1;
         ALLOC(g->code, u64, n);
         uint32_t* perm;
-        ALLOC(perm, uint32_t, n);
+        Temps tmp(g);
+        TALLOC(tmp, perm, uint32_t, n);
         Scratch s = scratch_of(g);
         CK(launch_morton(xyz_dev, n, g->origin, g->shift, g->code, perm, g->st));
         CK(radix_sort_pairs(g->code, perm, n, 3 * g->B, s, g->st));
         ALLOC(g->pos, int4, n);
         if (rgb_dev) ALLOC(g->rgb, uchar4, n);
         CK(launch_gather(xyz_dev, rgb_dev, nullptr, perm, n, g->pos, g->rgb, nullptr, g->st));
-        gfree(g, perm);
+        tmp.done(perm);
         ALLOC(g->leaf, uint8_t, n);
         ALLOC(g->alive, uint8_t, n);
         CK(cudaMemsetAsync(g->alive, 1, n, g->st));
         ALLOC(g->groups, int4, n);
         return build_cells(g);
     };
-    TRY(body());
+    rc = body();
+    cudaEventRecord(be1, g->st);
+    float bms = 0.f;
+    if (!rc && cudaEventSynchronize(be1) == cudaSuccess) cudaEventElapsedTime(&bms, be0, be1);
+    cudaEventDestroy(be0);
+    cudaEventDestroy(be1);
+    if (rc) return fail(rc);
 #undef TRY
+    g->ms_grid = bms;
+    g->stats.ms_grid = bms;
     *out = g;
     return PD_OK;
 }
@@ -484,8 +521,9 @@ int knn_all(pd_grid* g, const pd_cost_params* cp, double* cost_s) {
 // rebuild the cell table; stored neighbours are remapped (A7).
 int compact_rebuild(pd_grid* g, bool remap_state) {
     Scratch s = scratch_of(g);
+    Temps tmp(g);
     int* list;
-    ALLOC(list, int, g->ng);
+    TALLOC(tmp, list, int, g->ng);
     int* d_cnt = g->d_int + 2;
     CK(stable_compact(g->alive, g->ng, list, d_cnt, s, g->st));
     int nl = 0;
@@ -494,7 +532,7 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
     // the compacted arrays hold the live points only
     const int64_t cn = nl > 0 ? nl : 1;
     int* newpos;
-    ALLOC(newpos, int, g->ng);
+    TALLOC(tmp, newpos, int, g->ng);
     CK(cudaMemsetAsync(newpos, 0xff, g->ng * sizeof(int), g->st));  // -1: not kept
     CK(launch_newpos(list, nl, newpos, g->st));
     int4* pos2;
@@ -548,8 +586,8 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
         gfree(g, g->nbr);
         g->nbr = nb2;
     }
-    gfree(g, newpos);
-    gfree(g, list);
+    tmp.done(newpos);
+    tmp.done(list);
     g->ng = nl;
     CK(cudaMemsetAsync(g->alive, 1, nl, g->st));
     g->stats.grid_builds++;
@@ -578,8 +616,9 @@ Sel key_from_digits(const uint32_t* d, int npass) {
 
 int select_rank(pd_grid* g, const u64* prim, const uint8_t* alive, int64_t r, int64_t band_rank,
                 Sel* out, Sel* band_out) {
+    Temps tmp(g);
     uint32_t* hist;
-    ALLOC(hist, uint32_t, 4096);
+    TALLOC(tmp, hist, uint32_t, 4096);
     std::vector<uint32_t> h(4096);
     uint32_t pre[8] = {0};
     u64* bufA = nullptr;
@@ -625,23 +664,18 @@ int select_rank(pd_grid* g, const u64* prim, const uint8_t* alive, int64_t r, in
         int64_t nlen = h[b];
         u64* nb;
         int* ni;
-        ALLOC(nb, u64, nlen);
-        ALLOC(ni, int, nlen);
+        TALLOC(tmp, nb, u64, nlen);
+        TALLOC(tmp, ni, int, nlen);
         CK(launch_sel_compact(prim, g->pos, alive, g->ng, pass ? bufA : nullptr, idA, len, pass,
                               pre, nb, ni, d_cnt, g->st));
         if (bufA) {
-            gfree(g, bufA);
-            gfree(g, idA);
+            tmp.done(bufA);
+            tmp.done(idA);
         }
         bufA = nb;
         idA = ni;
         len = nlen;
     }
-    if (bufA) {
-        gfree(g, bufA);
-        gfree(g, idA);
-    }
-    gfree(g, hist);
     return rc;
 }
 
@@ -724,8 +758,9 @@ int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint
 // class are the first pops of the sequential greedy (their cost is +inf).
 int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
     *removed = 0;
+    Temps tmp(g);
     uint8_t* dup;
-    ALLOC(dup, uint8_t, g->ng);
+    TALLOC(tmp, dup, uint8_t, g->ng);
     CK(launch_dup_flag(g->code, g->pos, g->ng, dup, g->d_u64, g->st));
     unsigned long long nd = 0;
     CK(cudaMemcpyAsync(&nd, g->d_u64, sizeof(nd), cudaMemcpyDeviceToHost, g->st));
@@ -735,11 +770,11 @@ int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
         if ((int64_t)nd > need) {
             // the need largest input indices among the duplicates
             u64* zeros;
-            ALLOC(zeros, u64, g->ng);
+            TALLOC(tmp, zeros, u64, g->ng);
             CK(cudaMemsetAsync(zeros, 0, g->ng * sizeof(u64), g->st));
             Sel s;
             int rc = select_rank(g, zeros, dup, need, 0, &s, nullptr);
-            gfree(g, zeros);
+            tmp.done(zeros);
             if (rc) return rc;
             idx_min = s.idx;
             *removed = need;
@@ -748,7 +783,6 @@ int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
         }
         CK(launch_dup_remove(dup, g->pos, g->ng, idx_min, g->alive, g->st));
     }
-    gfree(g, dup);
     return PD_OK;
 }
 
@@ -788,6 +822,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     g->stats.leaf_max = g->T;
     g->stats.n = g->n;
     g->stats.m = m;
+    g->stats.ms_grid = g->ms_grid;
     long long launches0 = g_launch_count;
     RoundScratch rs(g);
     Timers T(g->st);
@@ -892,6 +927,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     int64_t built = live;
     while (live > m) {
         g->stats.rounds++;
+        g->stats.live_rounds += live;
         if (g->max_rounds && g->stats.rounds > g->max_rounds) {
             set_err(g->ctx, "pd_decimate: stopped after %s%lld rounds (PD_MAX_ROUNDS)", "",
                     (long long)g->max_rounds);
@@ -1037,6 +1073,7 @@ static int wup_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* ke
     g->stats.leaf_max = g->T;
     g->stats.n = g->n;
     g->stats.m = m;
+    g->stats.ms_grid = g->ms_grid;
     long long launches0 = g_launch_count;
     RoundScratch rs(g);
     Timers T(g->st);
@@ -1067,6 +1104,10 @@ static int wup_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* ke
     CK(cudaMemsetAsync(sb.hist, 0, 4096 * sizeof(uint32_t), g->st));
     RoundDev* rd;
     RALLOC(rd, RoundDev, 1);
+    u64* tmin;
+    int* imin;
+    RALLOC(tmin, u64, 1);
+    RALLOC(imin, int, 1);
     int64_t live = g->n, built = g->n;
     int iters = 0;
     while (live > m) {
@@ -1098,6 +1139,7 @@ static int wup_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* ke
         {
             Span t(T, &g->stats.ms_select);
             CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+            CK(wup_launch_exact_tau(g->prim, g->pos, g->alive, g->ng, rd, tmin, imin, g->st));
         }
         // 3. removal rounds above w_up
         for (int r = 0;; r++) {
@@ -1108,6 +1150,7 @@ static int wup_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* ke
                                g->st));
             CK(cudaStreamSynchronize(g->st));
             g->stats.rounds++;
+            g->stats.live_rounds += live;
             if ((int64_t)removed > live - m || (r == 0 && removed == 0)) {
                 set_err(g->ctx, "pd_decimate_wup: a round removed %s%lld points", "",
                         (long long)removed);
@@ -1147,12 +1190,13 @@ extern "C" int pd_knn_cost(pd_grid* g, const pd_cost_params* cp, double* cost_de
     }
     rc = prepare_state(g, cp);
     if (rc) return rc;
+    Temps tmp(g);
     double* cost_s;
-    ALLOC(cost_s, double, g->n);
+    TALLOC(tmp, cost_s, double, g->n);
     rc = knn_all(g, cp, cost_s);
     if (rc) return rc;
     CK(launch_knn_out(g->pos, cost_s, g->nbr, g->ng, g->S, cp->k, cost_dev, knn_dev, g->st));
-    gfree(g, cost_s);
+    tmp.done(cost_s);
     CK(cudaStreamSynchronize(g->st));
     return PD_OK;
 }

@@ -363,8 +363,11 @@ __device__ __forceinline__ void scan_range(const GridView& g, const KnnArgs& a, 
 }
 
 // Results of a query whose list is exact (one lane per query).
+// hzv: squared distance below which every live point is in the list (the
+// searched cube's gap and the skipped cells' boxes; the S-th distance when
+// the list is full).
 template <int S, int FILT, bool W, class TL>
-__device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& top) {
+__device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& top, u64 hzv) {
     int found = 0;
 #pragma unroll
     for (int i = 0; i < S; i++) found += top.has(i);
@@ -383,7 +386,10 @@ __device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& 
             a.prim_out[q] = key_prim_d2(d0);
             a.rk2_out[q] = d0;
             a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0) | (shell << 2));
-            if (a.hz_out) a.hz_out[q] = top.has(S - 1) ? top.dist(S - 1) : ~0ull;
+            if (a.hz_out) {
+                u64 h = top.has(S - 1) ? top.dist(S - 1) : ~0ull;
+                a.hz_out[q] = hzv < h ? hzv : h;
+            }
             if (a.cost_out) a.cost_out[q] = d0 == ~0ull ? 0.0 : __ddiv_rn(1.0, (double)d0);
         } else {
             int k = a.k;
@@ -423,6 +429,7 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
                                           int* so, unsigned long long& wpairs) {
     TL top;
     top.init();
+    u64 hzl = ~0ull;  // smallest box distance of a range this lane did not scan
     for (int r = 0; r < 27; r++) {
         int tr = __shfl_sync(FULLM, rt, r);
         if (!tr) continue;
@@ -431,11 +438,16 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
         int bxr = __shfl_sync(FULLM, bx, r), byr = __shfl_sync(FULLM, by, r),
             bzr = __shfl_sync(FULLM, bz, r);
         bool skip = true;
+        u64 bd = ~0ull;
         if (todo) {
             u64 bound = top.at(R - 1);
-            skip = bound != ~0ull && box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift) > bound;
+            bd = box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift);
+            skip = bound != ~0ull && bd > bound;
         }
-        if (__all_sync(FULLM, skip)) continue;
+        if (__all_sync(FULLM, skip)) {
+            if (bd < hzl) hzl = bd;
+            continue;
+        }
         if (a.pairs_out) {  // warp-uniform count of the pairs this range costs
             int nqt = __popc(__ballot_sync(FULLM, todo && sub == 0));
             wpairs += (unsigned long long)(e - b) * (unsigned long long)nqt;
@@ -454,7 +466,7 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
         u64 bound = top.at(R - 1);
         if (gg == ~0ull || bound < gg) {
             todo = false;
-            if (sub == 0) write_result<S, FILT, W>(a, q, top);
+            if (sub == 0) write_result<S, FILT, W>(a, q, top, hzl < gg ? hzl : gg);
         }
     }
 }
@@ -512,7 +524,7 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
     // full searches: all S stored neighbours exact (the k+b neighbour buffer,
     // so a removal can be absorbed without a new search; for the k = 1
     // density cost the nearest shell is then complete); filtered searches: k.
-    const int R = FILT == FILT_NONE ? S : a.k;
+    const int R = FILT == FILT_NONE ? (a.r_exact > 0 && a.r_exact < S ? a.r_exact : S) : a.k;
     bool todo = q >= 0;
     unsigned long long wpairs = 0;
     if (FILT == FILT_BELOW_TAU && a.hz_out) {

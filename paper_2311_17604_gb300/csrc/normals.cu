@@ -190,10 +190,14 @@ __device__ inline void mma16816(float c[4], const uint32_t a[4], uint32_t b0, ui
 #define MLP_WARPS 8
 #define MLP_BLOCKS_PER_SM 3
 
+// Weight rows are padded (56 and 72 bf16 = 28 and 36 words) so that the
+// eight row groups of a B-fragment load fall in distinct shared-memory banks.
+#define W1_LD 56
+#define W2_LD 72
 struct MlpSmem {
-    __nv_bfloat16 w1[NH * NF];
-    __nv_bfloat16 w2[NH * NH];
-    __nv_bfloat16 w3[8 * NH];  // rows 3..7 zero
+    __nv_bfloat16 w1[NH * W1_LD];
+    __nv_bfloat16 w2[NH * W2_LD];
+    __nv_bfloat16 w3[8 * W2_LD];  // rows 3..7 zero
     float b1[NH], b2[NH], b3[8];
 };
 
@@ -230,10 +234,12 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, MLP_BLOCKS_PER_SM)
                        const int* __restrict__ rows, int64_t n, float* outn, float* onorm,
                        float* h1s, float* h2s, float* raw) {
     __shared__ MlpSmem sm;
-    for (int i = threadIdx.x; i < NH * NF; i += blockDim.x) sm.w1[i] = __float2bfloat16_rn(prm[O_W1 + i]);
-    for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) sm.w2[i] = __float2bfloat16_rn(prm[O_W2 + i]);
+    for (int i = threadIdx.x; i < NH * NF; i += blockDim.x)
+        sm.w1[(i / NF) * W1_LD + i % NF] = __float2bfloat16_rn(prm[O_W1 + i]);
+    for (int i = threadIdx.x; i < NH * NH; i += blockDim.x)
+        sm.w2[(i / NH) * W2_LD + i % NH] = __float2bfloat16_rn(prm[O_W2 + i]);
     for (int i = threadIdx.x; i < 8 * NH; i += blockDim.x)
-        sm.w3[i] = __float2bfloat16_rn(i < 3 * NH ? prm[O_W3 + i] : 0.f);
+        sm.w3[(i / NH) * W2_LD + i % NH] = __float2bfloat16_rn(i < 3 * NH ? prm[O_W3 + i] : 0.f);
     for (int i = threadIdx.x; i < NH; i += blockDim.x) {
         sm.b1[i] = prm[O_B1 + i];
         sm.b2[i] = prm[O_B2 + i];
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, MLP_BLOCKS_PER_SM)
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const uint32_t* wr =
-                    reinterpret_cast<const uint32_t*>(sm.w1 + (8 * j + g) * NF + 16 * kk);
+                    reinterpret_cast<const uint32_t*>(sm.w1 + (8 * j + g) * W1_LD + 16 * kk);
                 mma16816(c1[j], a, wr[t], wr[4 + t]);
             }
         }
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, MLP_BLOCKS_PER_SM)
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const uint32_t* wr =
-                    reinterpret_cast<const uint32_t*>(sm.w2 + (8 * j + g) * NH + 16 * kk);
+                    reinterpret_cast<const uint32_t*>(sm.w2 + (8 * j + g) * W2_LD + 16 * kk);
                 mma16816(c2[j], a2[kk], wr[t], wr[4 + t]);
             }
         }
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, MLP_BLOCKS_PER_SM)
         float c3[4] = {sm.b3[2 * t], sm.b3[2 * t + 1], sm.b3[2 * t], sm.b3[2 * t + 1]};
 #pragma unroll
         for (int kk = 0; kk < 4; kk++) {
-            const uint32_t* wr = reinterpret_cast<const uint32_t*>(sm.w3 + g * NH + 16 * kk);
+            const uint32_t* wr = reinterpret_cast<const uint32_t*>(sm.w3 + g * W2_LD + 16 * kk);
             mma16816(c3, a3[kk], wr[t], wr[4 + t]);
         }
         // columns 0,1 sit on lane t = 0 and column 2 on t = 1 of each row
@@ -336,56 +342,90 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, MLP_BLOCKS_PER_SM)
     }
 }
 
-// ------------------------------------------------------------------ backward (float32)
-// Persistent over tiles of BW_ROWS rows.  Each thread owns the parameters
-// i = tid + 256 j and accumulates their gradient over all its block's tiles;
-// one atomic add per parameter and block at the end.  Weights enter as the
-// bfloat16 values the forward used; rounding is treated as the identity.
-#define BW_ROWS 32
-#define BW_THREADS 256
-#define BW_PER_THREAD ((N_PARAMS + BW_THREADS - 1) / BW_THREADS)
-__global__ void __launch_bounds__(BW_THREADS)
-    mlp_backward_kernel(const float* __restrict__ prm, const uint16_t* __restrict__ feat,
-                        const int* __restrict__ rows, const float* __restrict__ labels, int64_t n,
-                        const float* __restrict__ h1s, const float* __restrict__ h2s,
-                        const float* __restrict__ raw, float* __restrict__ part) {
-    __shared__ float sx[BW_ROWS][NF];
-    __shared__ float sh1[BW_ROWS][NH];
-    __shared__ float sh2[BW_ROWS][NH];
-    __shared__ float sd1[BW_ROWS][NH];
-    __shared__ float sd2[BW_ROWS][NH];
-    __shared__ float sdo[BW_ROWS][3];
-    __shared__ __nv_bfloat16 w2b[NH * NH];
-    __shared__ float w3b[3][NH];
-    const int tid = threadIdx.x;
+// ------------------------------------------------------------------ backward (tensor cores)
+// Persistent over tiles of TR = 64 rows; 4 warps per block, warp w owning
+// rows 16w..16w+15 of a tile for the row-wise products and the 16-row slice
+// w of the weight gradients.  All matrix products run as mma.sync m16n8k16
+// (bf16 in, fp32 accumulate):
+//   dh1 = (dh2 W2) relu'(h1)            A = dh2 [row][j], B = W2 (as W2^T [c][j])
+//   dW2 = dh2^T h1                       A = dh2^T [j][row], B = h1 (as h1^T [c][row])
+//   dW1 = dh1^T x                        A = dh1^T [a][row], B = x (as x^T [f][row])
+// x, h1 and the weights are bfloat16 values already (what the forward used).
+// The gradients dh1 and dh2 are float32: each enters as the sum of two
+// bfloat16 parts hi + lo (hi = bf16(v), lo = bf16(v - hi)), two products per
+// tile, so the result keeps about 16 bits of the float32 value.  The small
+// pieces (dh2 = do W3 masked, dW3, the biases, the loss) run on the CUDA
+// cores.  Weights enter as the bfloat16 values the forward used; rounding is
+// treated as the identity (a straight-through gradient).
+#define BT_ROWS 64
+#define BT_THREADS 128
+#define BT_LD 72  // row stride (bf16) of the shared tiles: 144 bytes
+#define BT_BLOCKS_PER_SM 2
+
+struct BwSmem {
+    __nv_bfloat16 w2t[NH][BT_LD];      // W2^T [c][j]
+    __nv_bfloat16 xt[NF][BT_LD];       // x^T  [f][row]
+    __nv_bfloat16 h1t[NH][BT_LD];      // h1^T [c][row]
+    __nv_bfloat16 d2[2][BT_ROWS][BT_LD];   // dh2 [row][j], hi and lo
+    __nv_bfloat16 d2t[2][NH][BT_LD];       // dh2^T [j][row], hi and lo
+    __nv_bfloat16 d1t[2][NH][BT_LD];       // dh1^T [a][row], hi and lo
+    float w3[3][NH];
+    float dout[BT_ROWS][4];            // d loss / d o (divided by n)
+    float red[BT_THREADS][4];          // end-of-kernel reductions
+    float db1w[4][NH];                 // per-warp column sums of dh1
+};
+
+__device__ inline uint32_t ld32(const __nv_bfloat16* p) {
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__global__ void __launch_bounds__(BT_THREADS, BT_BLOCKS_PER_SM)
+    mlp_backward_tc_kernel(const float* __restrict__ prm, const uint16_t* __restrict__ feat,
+                           const int* __restrict__ rows, const float* __restrict__ labels,
+                           int64_t n, const float* __restrict__ h1s,
+                           const float* __restrict__ h2s, const float* __restrict__ raw,
+                           float* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    BwSmem& sm = *reinterpret_cast<BwSmem*>(smraw);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     const float inv_n = 1.0f / (float)n;
-    for (int i = tid; i < NH * NH; i += BW_THREADS) w2b[i] = __float2bfloat16_rn(prm[O_W2 + i]);
-    for (int i = tid; i < 3 * NH; i += BW_THREADS)
-        w3b[i / NH][i % NH] = __bfloat162float(__float2bfloat16_rn(prm[O_W3 + i]));
-    float acc[BW_PER_THREAD];
+    for (int i = tid; i < NH * NH; i += BT_THREADS) {
+        int j = i / NH, c = i % NH;  // W2 is [j][c] (out, in)
+        sm.w2t[c][j] = __float2bfloat16_rn(prm[O_W2 + i]);
+    }
+    for (int i = tid; i < 3 * NH; i += BT_THREADS)
+        sm.w3[i / NH][i % NH] = __bfloat162float(__float2bfloat16_rn(prm[O_W3 + i]));
+    // accumulators: dW1 rows a = 16w.. (6 n-tiles of f), dW2 rows j = 16w.. (8 n-tiles of c)
+    float g1[6][4], g2[8][4];
 #pragma unroll
-    for (int j = 0; j < BW_PER_THREAD; j++) acc[j] = 0.f;
-    float lsum = 0.f;
-    const int64_t ntiles = (n + BW_ROWS - 1) / BW_ROWS;
+    for (int i = 0; i < 6; i++) g1[i][0] = g1[i][1] = g1[i][2] = g1[i][3] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; i++) g2[i][0] = g2[i][1] = g2[i][2] = g2[i][3] = 0.f;
+    float db1[16];  // columns 8 nt + 2 t (+1) of dh1, this lane's rows
+#pragma unroll
+    for (int i = 0; i < 16; i++) db1[i] = 0.f;
+    float db2 = 0.f, dw3[3] = {0.f, 0.f, 0.f}, db3[3] = {0.f, 0.f, 0.f}, lsum = 0.f;
+    const int jcol = tid & 63;  // the dh2 column this thread computes
+    const int64_t ntiles = (n + BT_ROWS - 1) / BT_ROWS;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * BW_ROWS;
-        const int nr = (int)min((int64_t)BW_ROWS, n - r0);
-        __syncthreads();  // previous tile's readers are done
-        for (int i = tid; i < BW_ROWS * NF; i += BW_THREADS) {
+        const int64_t r0 = tile * BT_ROWS;
+        const int nr = (int)min((int64_t)BT_ROWS, n - r0);
+        __syncthreads();  // the previous tile's readers are done
+        for (int i = tid; i < BT_ROWS * NF; i += BT_THREADS) {
             int r = i / NF, f = i % NF;
-            float v = 0.f;
+            uint16_t v = 0;
             if (r < nr) {
                 int64_t x = rows ? rows[r0 + r] : r0 + r;
-                v = __bfloat162float(__ushort_as_bfloat16(feat[x * NF + f]));
+                v = feat[x * NF + f];
             }
-            sx[r][f] = v;
+            sm.xt[f][r] = __ushort_as_bfloat16(v);
         }
-        for (int i = tid; i < BW_ROWS * NH; i += BW_THREADS) {
+        for (int i = tid; i < BT_ROWS * NH; i += BT_THREADS) {
             int r = i / NH, c = i % NH;
-            sh1[r][c] = r < nr ? h1s[(r0 + r) * NH + c] : 0.f;
-            sh2[r][c] = r < nr ? h2s[(r0 + r) * NH + c] : 0.f;
+            float v = r < nr ? h1s[(r0 + r) * NH + c] : 0.f;
+            sm.h1t[c][r] = __float2bfloat16_rn(v);  // exact: h1 holds bfloat16 values
         }
-        if (tid < BW_ROWS) {  // d loss / d o, already divided by n
+        if (tid < BT_ROWS) {  // d loss / d o for row tid, already divided by n
             int r = tid;
             float d0 = 0.f, d1 = 0.f, d2 = 0.f;
             if (r < nr) {
@@ -398,70 +438,179 @@ __global__ void __launch_bounds__(BW_THREADS)
                     float dot = u0 * y0 + u1 * y1 + u2 * y2;
                     lsum += 1.f - dot * dot;
                     // dL/du = -2 dot y; dL/do = (dL/du - (dL/du . u) u) / |o|
-                    float g0 = -2.f * dot * y0, g1 = -2.f * dot * y1, g2 = -2.f * dot * y2;
-                    float gu = g0 * u0 + g1 * u1 + g2 * u2;
+                    float q0 = -2.f * dot * y0, q1 = -2.f * dot * y1, q2 = -2.f * dot * y2;
+                    float gu = q0 * u0 + q1 * u1 + q2 * u2;
                     float sc = inv_n / nrm;
-                    d0 = (g0 - gu * u0) * sc;
-                    d1 = (g1 - gu * u1) * sc;
-                    d2 = (g2 - gu * u2) * sc;
+                    d0 = (q0 - gu * u0) * sc;
+                    d1 = (q1 - gu * u1) * sc;
+                    d2 = (q2 - gu * u2) * sc;
                 }
             }
-            sdo[r][0] = d0;
-            sdo[r][1] = d1;
-            sdo[r][2] = d2;
+            sm.dout[r][0] = d0;
+            sm.dout[r][1] = d1;
+            sm.dout[r][2] = d2;
+            db3[0] += d0;
+            db3[1] += d1;
+            db3[2] += d2;
         }
         __syncthreads();
-        for (int i = tid; i < BW_ROWS * NH; i += BW_THREADS) {  // dh2 = (do W3) relu'(h2)
-            int r = i / NH, j = i % NH;
-            float v = sdo[r][0] * w3b[0][j] + sdo[r][1] * w3b[1][j] + sdo[r][2] * w3b[2][j];
-            sd2[r][j] = sh2[r][j] > 0.f ? v : 0.f;
-        }
-        __syncthreads();
-        for (int i = tid; i < BW_ROWS * NH; i += BW_THREADS) {  // dh1 = (dh2 W2) relu'(h1)
-            int r = i / NH, c = i % NH;
+        // dh2 = (do W3) relu'(h2): thread (jcol, rows tid/64 + 2i); dW3 and db2 on the side
+        for (int r = tid >> 6; r < BT_ROWS; r += BT_THREADS / 64) {
             float v = 0.f;
-#pragma unroll 8
-            for (int j = 0; j < NH; j++) v += sd2[r][j] * __bfloat162float(w2b[j * NH + c]);
-            sd1[r][c] = sh1[r][c] > 0.f ? v : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int jj = 0; jj < BW_PER_THREAD; jj++) {
-            int i = tid + BW_THREADS * jj;
-            float v = 0.f;
-            if (i < O_B1) {
-                int a = i / NF, f = i % NF;
-                for (int r = 0; r < nr; r++) v += sd1[r][a] * sx[r][f];
-            } else if (i < O_W2) {
-                int a = i - O_B1;
-                for (int r = 0; r < nr; r++) v += sd1[r][a];
-            } else if (i < O_B2) {
-                int j = (i - O_W2) / NH, c = (i - O_W2) % NH;
-                for (int r = 0; r < nr; r++) v += sd2[r][j] * sh1[r][c];
-            } else if (i < O_W3) {
-                int j = i - O_B2;
-                for (int r = 0; r < nr; r++) v += sd2[r][j];
-            } else if (i < O_B3) {
-                int c = (i - O_W3) / NH, j = (i - O_W3) % NH;
-                for (int r = 0; r < nr; r++) v += sdo[r][c] * sh2[r][j];
-            } else if (i < N_PARAMS) {
-                int c = i - O_B3;
-                for (int r = 0; r < nr; r++) v += sdo[r][c];
+            if (r < nr) {
+                float h2 = h2s[(r0 + r) * NH + jcol];
+                float d0 = sm.dout[r][0], d1 = sm.dout[r][1], d2 = sm.dout[r][2];
+                dw3[0] += d0 * h2;
+                dw3[1] += d1 * h2;
+                dw3[2] += d2 * h2;
+                v = d0 * sm.w3[0][jcol] + d1 * sm.w3[1][jcol] + d2 * sm.w3[2][jcol];
+                if (!(h2 > 0.f)) v = 0.f;
             }
-            acc[jj] += v;
+            db2 += v;
+            __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            sm.d2[0][r][jcol] = hi;
+            sm.d2[1][r][jcol] = lo;
+            sm.d2t[0][jcol][r] = hi;
+            sm.d2t[1][jcol][r] = lo;
+        }
+        __syncthreads();
+        // dh1 = (dh2 W2) relu'(h1) for rows 16w.. of the tile (tensor cores)
+        {
+            float acc[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+            const int ra = 16 * w + g, rb = ra + 8;
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) {
+#pragma unroll
+                for (int part_ = 0; part_ < 2; part_++) {
+                    uint32_t a[4];
+                    a[0] = ld32(&sm.d2[part_][ra][16 * kk + 2 * t]);
+                    a[1] = ld32(&sm.d2[part_][rb][16 * kk + 2 * t]);
+                    a[2] = ld32(&sm.d2[part_][ra][16 * kk + 8 + 2 * t]);
+                    a[3] = ld32(&sm.d2[part_][rb][16 * kk + 8 + 2 * t]);
+#pragma unroll
+                    for (int nt = 0; nt < 8; nt++) {
+                        uint32_t b0 = ld32(&sm.w2t[8 * nt + g][16 * kk + 2 * t]);
+                        uint32_t b1 = ld32(&sm.w2t[8 * nt + g][16 * kk + 8 + 2 * t]);
+                        mma16816(acc[nt], a, b0, b1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    int r = (e & 2) ? rb : ra;
+                    int c = 8 * nt + 2 * t + (e & 1);
+                    float v = acc[nt][e];
+                    if (!(__bfloat162float(sm.h1t[c][r]) > 0.f)) v = 0.f;
+                    db1[2 * nt + (e & 1)] += v;
+                    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                    sm.d1t[0][c][r] = hi;
+                    sm.d1t[1][c][r] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                }
+            }
+        }
+        __syncthreads();
+        // weight gradients over the tile's rows (K = 64): slice w of dW1 and dW2
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            const int ma = 16 * w + g, mb = ma + 8;
+#pragma unroll
+            for (int part_ = 0; part_ < 2; part_++) {
+                uint32_t a1[4], a2[4];
+                a1[0] = ld32(&sm.d1t[part_][ma][16 * kk + 2 * t]);
+                a1[1] = ld32(&sm.d1t[part_][mb][16 * kk + 2 * t]);
+                a1[2] = ld32(&sm.d1t[part_][ma][16 * kk + 8 + 2 * t]);
+                a1[3] = ld32(&sm.d1t[part_][mb][16 * kk + 8 + 2 * t]);
+                a2[0] = ld32(&sm.d2t[part_][ma][16 * kk + 2 * t]);
+                a2[1] = ld32(&sm.d2t[part_][mb][16 * kk + 2 * t]);
+                a2[2] = ld32(&sm.d2t[part_][ma][16 * kk + 8 + 2 * t]);
+                a2[3] = ld32(&sm.d2t[part_][mb][16 * kk + 8 + 2 * t]);
+#pragma unroll
+                for (int nt = 0; nt < 6; nt++) {
+                    uint32_t b0 = ld32(&sm.xt[8 * nt + g][16 * kk + 2 * t]);
+                    uint32_t b1 = ld32(&sm.xt[8 * nt + g][16 * kk + 8 + 2 * t]);
+                    mma16816(g1[nt], a1, b0, b1);
+                }
+#pragma unroll
+                for (int nt = 0; nt < 8; nt++) {
+                    uint32_t b0 = ld32(&sm.h1t[8 * nt + g][16 * kk + 2 * t]);
+                    uint32_t b1 = ld32(&sm.h1t[8 * nt + g][16 * kk + 8 + 2 * t]);
+                    mma16816(g2[nt], a2, b0, b1);
+                }
+            }
         }
     }
     // this block's partial sums; grad_reduce_kernel adds the blocks in a fixed
     // order, so the gradient is the same bit for bit on every run
     float* mine = part + (int64_t)blockIdx.x * (N_PARAMS + 1);
+    {
+        const int ma = 16 * w + g, mb = ma + 8;
 #pragma unroll
-    for (int jj = 0; jj < BW_PER_THREAD; jj++) {
-        int i = tid + BW_THREADS * jj;
-        if (i < N_PARAMS) mine[i] = acc[jj];
+        for (int nt = 0; nt < 6; nt++) {
+            int f = 8 * nt + 2 * t;
+            mine[O_W1 + ma * NF + f] = g1[nt][0];
+            mine[O_W1 + ma * NF + f + 1] = g1[nt][1];
+            mine[O_W1 + mb * NF + f] = g1[nt][2];
+            mine[O_W1 + mb * NF + f + 1] = g1[nt][3];
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            int c = 8 * nt + 2 * t;
+            mine[O_W2 + ma * NH + c] = g2[nt][0];
+            mine[O_W2 + ma * NH + c + 1] = g2[nt][1];
+            mine[O_W2 + mb * NH + c] = g2[nt][2];
+            mine[O_W2 + mb * NH + c + 1] = g2[nt][3];
+        }
     }
-    if (tid < 32) {
-        for (int off = 16; off; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-        if (tid == 0) mine[N_PARAMS] = lsum * inv_n;
+    // db1: sum this lane's rows over the 8 lanes of equal t, then the 4 warps
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        float v = db1[i];
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        db1[i] = v;
+    }
+    if (g == 0) {
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            sm.db1w[w][8 * nt + 2 * t] = db1[2 * nt];
+            sm.db1w[w][8 * nt + 2 * t + 1] = db1[2 * nt + 1];
+        }
+    }
+    __syncthreads();
+    if (tid < NH) {
+        float v = 0.f;
+        for (int ww = 0; ww < 4; ww++) v += sm.db1w[ww][tid];
+        mine[O_B1 + tid] = v;
+    }
+    __syncthreads();
+    // db2, dW3: two threads per column (tid and tid + 64)
+    sm.red[tid][0] = db2;
+    sm.red[tid][1] = dw3[0];
+    sm.red[tid][2] = dw3[1];
+    sm.red[tid][3] = dw3[2];
+    __syncthreads();
+    if (tid < NH) {
+        mine[O_B2 + tid] = sm.red[tid][0] + sm.red[tid + 64][0];
+        for (int c = 0; c < 3; c++) mine[O_W3 + c * NH + tid] = sm.red[tid][1 + c] + sm.red[tid + 64][1 + c];
+    }
+    __syncthreads();
+    // db3 and the loss: rows tid < 64
+    sm.red[tid][0] = db3[0];
+    sm.red[tid][1] = db3[1];
+    sm.red[tid][2] = db3[2];
+    sm.red[tid][3] = lsum;
+    __syncthreads();
+    if (tid < 4) {
+        float v = 0.f;
+        for (int r = 0; r < BT_ROWS; r++) v += sm.red[r][tid];
+        if (tid < 3) mine[O_B3 + tid] = v;
+        else mine[N_PARAMS] = v * inv_n;
     }
 }
 
@@ -575,7 +724,9 @@ cudaError_t launch_mlp_forward(const float* prm, const uint16_t* feat, const int
     return cudaGetLastError();
 }
 
-int64_t mlp_backward_part_floats() { return (int64_t)sm_count() * (N_PARAMS + 1); }
+static int64_t bt_blocks() { return (int64_t)sm_count() * BT_BLOCKS_PER_SM; }
+
+int64_t mlp_backward_part_floats() { return bt_blocks() * (N_PARAMS + 1); }
 
 cudaError_t launch_mlp_backward(const float* prm, const uint16_t* feat, const int* rows,
                                 const float* labels, int64_t n, const float* h1s,
@@ -586,11 +737,16 @@ cudaError_t launch_mlp_backward(const float* prm, const uint16_t* feat, const in
         if (!e) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
         return e;
     }
-    int64_t tiles = (n + BW_ROWS - 1) / BW_ROWS;
-    int64_t sms = sm_count();
-    int64_t blocks = tiles < sms ? tiles : sms;
-    mlp_backward_kernel<<<(unsigned)blocks, BW_THREADS, 0, st>>>(prm, feat, rows, labels, n, h1s,
-                                                                 h2s, raw, part);
+    static_assert(sizeof(BwSmem) <= 227 * 1024 / BT_BLOCKS_PER_SM, "backward shared memory");
+    cudaError_t e = cudaFuncSetAttribute(mlp_backward_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(BwSmem));
+    if (e) return e;
+    int64_t tiles = (n + BT_ROWS - 1) / BT_ROWS;
+    int64_t cap = bt_blocks();
+    int64_t blocks = tiles < cap ? tiles : cap;
+    mlp_backward_tc_kernel<<<(unsigned)blocks, BT_THREADS, sizeof(BwSmem), st>>>(
+        prm, feat, rows, labels, n, h1s, h2s, raw, part);
     note_launch();
     grad_reduce_kernel<<<(N_PARAMS + 1 + 255) / 256, 256, 0, st>>>(part, (int)blocks, grad, loss);
     note_launch();

@@ -124,6 +124,9 @@ struct KnnArgs {
                               //   32-position chunk (chunks above the threshold are skipped)
     const int* glist;         // group-list mode: process groups glist[0 .. *gcount)
     const int* gcount;        //   (device count; a persistent grid walks the list)
+    int r_exact;              // full searches: nearest entries that must be exact
+                              //   (0 = all S; the k = 1 density cost re-searches
+                              //   with 1 and keeps the rest below the horizon)
 };
 // Flagged mode without a host read: list the groups that hold a flagged query
 // (a.qflag), then run the search over that list only.  glist: ngroups ints,
@@ -234,6 +237,10 @@ cudaError_t launch_normal_fallback(const float* mlp, const float* onorm, const f
 // selection of w_up, then run one removal round (marks, picks, removal,
 // stored-list update).  S <= 8, k <= S.
 cudaError_t wup_launch_setup(RoundDev* rd, cudaStream_t st);
+// Replace the selection's bin boundary by the smallest live key at or above
+// it (the exact rank-th largest key).  tmin, imin: device scratch words.
+cudaError_t wup_launch_exact_tau(const u64* prim, const int4* pos, const uint8_t* alive,
+                                 int64_t n, RoundDev* rd, u64* tmin, int* imin, cudaStream_t st);
 cudaError_t wup_launch_round(const BufView& b, uint8_t* alive, uint8_t* wdirty, int64_t n, int S,
                              int k, RoundDev* rd, u64* mark_p, int* mark_i, uint8_t* pick,
                              cudaStream_t st);

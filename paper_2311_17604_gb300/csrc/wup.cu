@@ -49,6 +49,36 @@ __global__ void wup_setup_kernel(RoundDev* rd) {
     rd->overflow = 0;
 }
 
+// The key selection returns the lower boundary of the bin that holds the
+// rank-th largest key, which counts the same keys but is not a key itself;
+// w_up stays fixed while keys fall during an iteration, so it must be the
+// key: the smallest live key at or above that boundary (two passes, primary
+// then index).
+__global__ void wup_tau_min_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
+                                   const uint8_t* __restrict__ alive, int64_t n,
+                                   const RoundDev* rd, u64* tmin) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n || !alive[s]) return;
+    u64 p = prim[s];
+    if (!key_gt(rd->tau_prim, rd->tau_idx, p, pos[s].w)) atomicMin(tmin, p);
+}
+
+__global__ void wup_tau_min2_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
+                                    const uint8_t* __restrict__ alive, int64_t n,
+                                    const RoundDev* rd, const u64* tmin, int* imin) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n || !alive[s]) return;
+    u64 p = prim[s];
+    int i = pos[s].w;
+    if (p == *tmin && !key_gt(rd->tau_prim, rd->tau_idx, p, i)) atomicMin(imin, i);
+}
+
+__global__ void wup_tau_set_kernel(RoundDev* rd, const u64* tmin, const int* imin) {
+    if (threadIdx.x != 0) return;
+    rd->tau_prim = *tmin;
+    rd->tau_idx = *imin;
+}
+
 __global__ void wup_round_reset_kernel(RoundDev* rd) {
     if (threadIdx.x != 0) return;
     rd->ncand = 0;
@@ -168,6 +198,22 @@ __global__ void wup_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
 cudaError_t wup_launch_setup(RoundDev* rd, cudaStream_t st) {
     wup_setup_kernel<<<1, 32, 0, st>>>(rd);
     note_launch();
+    return cudaGetLastError();
+}
+
+// w_up as a key: tau <- the smallest live key >= the selection's boundary.
+// tw: one u64 and one int of device scratch.
+cudaError_t wup_launch_exact_tau(const u64* prim, const int4* pos, const uint8_t* alive,
+                                 int64_t n, RoundDev* rd, u64* tmin, int* imin,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(tmin, 0xff, sizeof(u64), st);
+    if (!e) e = cudaMemsetAsync(imin, 0x7f, sizeof(int), st);
+    if (e) return e;
+    wup_tau_min_kernel<<<WGRID(n), 0, st>>>(prim, pos, alive, n, rd, tmin);
+    wup_tau_min2_kernel<<<WGRID(n), 0, st>>>(prim, pos, alive, n, rd, tmin, imin);
+    wup_tau_set_kernel<<<1, 32, 0, st>>>(rd, tmin, imin);
+    for (int i = 0; i < 3; i++) note_launch();
     return cudaGetLastError();
 }
 
