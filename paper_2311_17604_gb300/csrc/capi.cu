@@ -133,6 +133,7 @@ struct pd_grid {
     std::vector<void*> owned;
     pd_stats stats;
     double ms_grid;  // device time of the pd_build_grid call
+    int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8)
     int trace;       // PD_TRACE set: one line per removal round on stderr
     int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
 };
@@ -327,6 +328,9 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     g->st = (cudaStream_t)stream;
     g->trace = getenv("PD_TRACE") != nullptr;
     g->max_rounds = getenv("PD_MAX_ROUNDS") ? atoi(getenv("PD_MAX_ROUNDS")) : 0;
+    // diagnostic: exact depth of the k = 1 searches (any depth gives the same
+    // result; the stored list is complete below the reported horizon)
+    g->k1_exact = getenv("PD_K1_EXACT") ? atoi(getenv("PD_K1_EXACT")) : 0;
     g->n = n;
     g->ng = n;
     g->T = T;
@@ -467,6 +471,7 @@ KnnArgs base_args(pd_grid* g, const pd_cost_params* cp) {
     a.flg_out = g->flg;
     a.hz_out = g->hz;
     a.cmin = g->cmin;
+    if (g->density_k1 && g->k1_exact > 0) a.r_exact = g->k1_exact;
     return a;
 }
 
@@ -982,11 +987,18 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         } else {
             CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
         }
+        cudaEvent_t tq0 = nullptr, tq1 = nullptr;  // trace only: this round's re-search time
+        if (g->trace) {
+            cudaEventCreate(&tq0);
+            cudaEventCreate(&tq1);
+            cudaEventRecord(tq0, g->st);
+        }
         {
             Span t(T, &g->stats.ms_knn_requery);
             rc = knn_flag(g, cp, FILT_NONE, S, dirty, nullptr, rd);
             if (rc) return rc;
         }
+        if (g->trace) cudaEventRecord(tq1, g->st);
         CK(round_launch_finish(rd, g->st));
         CK(cudaMemcpyAsync(&h, rd, sizeof(h), cudaMemcpyDeviceToHost, g->st));
         CK(cudaStreamSynchronize(g->st));
@@ -1014,11 +1026,18 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             CK(cudaMemcpyAsync(&rd->tot_requery, &h.tot_requery, sizeof(u64),
                                cudaMemcpyHostToDevice, g->st));
         }
-        if (g->trace)
+        if (g->trace) {
+            float rq_ms = 0.f;
+            cudaEventSynchronize(tq1);
+            cudaEventElapsedTime(&rq_ms, tq0, tq1);
+            cudaEventDestroy(tq0);
+            cudaEventDestroy(tq1);
             fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu band %.3g "
-                    "sources %d pairs %d cap-over %llu%s\n", g->stats.rounds, (long long)live,
-                    (long long)(live - m), h.ncand, h.removed, h.band, h.nsrc, h.npairs,
-                    h.cap_over, h.overflow ? " overflow" : (h.fix_unconverged ? " unconverged" : ""));
+                    "sources %d pairs %d cap-over %llu requeries %llu (%.2f ms)%s\n",
+                    g->stats.rounds, (long long)live, (long long)(live - m), h.ncand, h.removed,
+                    h.band, h.nsrc, h.npairs, h.cap_over, h.tot_requery, rq_ms,
+                    h.overflow ? " overflow" : (h.fix_unconverged ? " unconverged" : ""));
+        }
         if (h.removed == 0 || (int64_t)h.removed > live - m) {
             set_err(g->ctx, "pd_decimate: round removed %s%lld points", "", (long long)h.removed);
             return PD_EINTERNAL;
