@@ -134,6 +134,9 @@ struct pd_grid {
     pd_stats stats;
     double ms_grid;  // device time of the pd_build_grid call
     int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8)
+    int sparse_rq;   // re-searches over a list of the flagged points, 4 lanes each (else per group)
+    int* rq_list;    // during a decimation: flagged Morton positions and their count
+    int* rq_count;
     int trace;       // PD_TRACE set: one line per removal round on stderr
     int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
 };
@@ -331,6 +334,8 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     // diagnostic: exact depth of the k = 1 searches (any depth gives the same
     // result; the stored list is complete below the reported horizon)
     g->k1_exact = getenv("PD_K1_EXACT") ? atoi(getenv("PD_K1_EXACT")) : 0;
+    // diagnostic: 0 runs the re-searches per leaf group (same results)
+    g->sparse_rq = getenv("PD_SPARSE_REQUERY") ? atoi(getenv("PD_SPARSE_REQUERY")) : 1;
     g->n = n;
     g->ng = n;
     g->T = T;
@@ -710,6 +715,12 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
     a.rd = rd;
     if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
     if (filter == FILT_BELOW_TAU) a.lam_out = fout;
+    if (filter == FILT_NONE && g->sparse_rq && g->rq_list) {
+        // re-searches: the flagged points, listed, 4 lanes each over their own cells
+        CK(stable_compact(qflag, g->ng, g->rq_list, g->rq_count, scratch_of(g), g->st));
+        CK(launch_knn_sparse(view_of(g), a, g->rq_list, g->rq_count, g->ng, g->st));
+        return PD_OK;
+    }
     if (!g->glist) {  // groups never outnumber the points of the first build
         ALLOC(g->glist, int, g->n);
         ALLOC(g->gcount, int, 1);
@@ -802,6 +813,8 @@ struct RoundScratch {
         for (void* p : ptrs) gfree(g, p);
         gfree(g, g->cmin);
         g->cmin = nullptr;
+        g->rq_list = nullptr;  // released with ptrs
+        g->rq_count = nullptr;
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     }
@@ -889,6 +902,10 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     RALLOC(inP, uint8_t, cap);
     RALLOC(rej, uint8_t, cap);
     RALLOC(dirty, uint8_t, cap);
+    if (g->sparse_rq) {
+        RALLOC(g->rq_list, int, cap);
+        RALLOC(g->rq_count, int, 1);
+    }
     RALLOC(cand, int, cap);
     RALLOC(slow, int, cap);
     CK(cudaMemsetAsync(inP, 0, cap, g->st));

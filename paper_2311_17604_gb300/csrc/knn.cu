@@ -593,6 +593,113 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
     }
 }
 
+// Sparse re-searches: the listed queries (Morton positions, list[0 .. *count))
+// run 8 to a warp, 4 lanes per query, each query over the 3x3x3 cells of its
+// own leaf level.  The 4 lanes resolve the same cells and split every range
+// (lane sub takes positions b + sub, b + sub + 4, ...), each keeping a partial
+// list; the partial lists merge once per level.  A lane skips a range whose
+// box lies beyond its own partial bound (never closer than the merged one),
+// and the smallest box distance it skipped bounds the reported horizon.
+// Used for the re-searches of the removal rounds, where the flagged queries
+// are few per leaf group and a warp per group would idle most lanes.
+#define SP_LANES 4
+
+template <int S, bool W>
+__global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, KnnArgs a,
+                                                                  const int* __restrict__ list,
+                                                                  const int* __restrict__ count) {
+    const int lane = threadIdx.x & 31, sub = lane & (SP_LANES - 1);
+    const int nq = *count;
+    const int per_warp = 32 / SP_LANES;
+    const int wid = blockIdx.x * PD_WARPS + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * PD_WARPS;
+    const int R = a.r_exact > 0 && a.r_exact < S ? a.r_exact : S;
+    for (int base = wid * per_warp; base < nq; base += nwarps * per_warp) {  // warp-uniform
+        const int slot = base + lane / SP_LANES;
+        const int q = slot < nq ? list[slot] : -1;
+        bool todo = q >= 0;
+        int4 qp = make_int4(0, 0, 0, 0);
+        u64 c0 = 0;
+        int L = 0;
+        if (todo) {
+            qp = g.pos[q];
+            c0 = g.code[q];
+            L = g.leaf[q];
+        }
+        const int ux = qp.x - g.origin.x, uy = qp.y - g.origin.y, uz = qp.z - g.origin.z;
+        while (__any_sync(FULLM, todo)) {
+            TopList<S, W> top;
+            top.init();
+            u64 hzl = ~0ull;
+            int cx = 0, cy = 0, cz = 0;
+            if (todo) {
+                if (L < g.B) {
+                    cx = (int)compact3(c0 >> (3 * L));
+                    cy = (int)compact3(c0 >> (3 * L + 1));
+                    cz = (int)compact3(c0 >> (3 * L + 2));
+                }
+                const int lim = 1 << (g.B - L);
+                for (int r = 0; r < 27; r++) {
+                    int o = kCellOrder[r];
+                    int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                    uint32_t b, e;
+                    int rl = L;
+                    int rt = resolve_cell(g, L, cx + dx, cy + dy, cz + dz, b, e, &rl);
+                    if (!rt) continue;
+                    if (rt == 2) {
+                        // a coarse leaf covers every cell whose coordinates agree with
+                        // this one's above level rl: scan it from the first such cell only
+                        const int sh = rl - L;
+                        bool dup = false;
+                        for (int r2 = 0; r2 < r && !dup; r2++) {
+                            int o2 = kCellOrder[r2];
+                            int ex = cx + o2 % 3 - 1, ey = cy + (o2 / 3) % 3 - 1, ez = cz + o2 / 9 - 1;
+                            if (ex < 0 || ey < 0 || ez < 0 || ex >= lim || ey >= lim || ez >= lim)
+                                continue;
+                            dup = (ex >> sh) == ((cx + dx) >> sh) && (ey >> sh) == ((cy + dy) >> sh) &&
+                                  (ez >> sh) == ((cz + dz) >> sh);
+                        }
+                        if (dup) continue;
+                    }
+                    int bxr = (cx + dx) >> (rl - L), byr = (cy + dy) >> (rl - L),
+                        bzr = (cz + dz) >> (rl - L);
+                    u64 bd = box_d2(ux, uy, uz, bxr, byr, bzr, rl + g.shift);
+                    u64 bound = top.at(R - 1);
+                    if (bound != ~0ull && bd > bound) {
+                        if (bd < hzl) hzl = bd;
+                        continue;
+                    }
+                    for (uint32_t j = b + sub; j < e; j += SP_LANES) {
+                        if ((int)j == q) continue;
+                        if (a.alive && !a.alive[j]) continue;
+                        int4 v = g.pos[j];
+                        long long ddx = (long long)v.x - qp.x, ddy = (long long)v.y - qp.y,
+                                  ddz = (long long)v.z - qp.z;
+                        u64 dd = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
+                        int co = W ? v.w : (int)j;
+                        if (top.beats_last(dd, (int)j, co)) top.insert(dd, (int)j, co);
+                    }
+                }
+            }
+            // merge the 4 partial lists and horizons of each query (all lanes take part)
+            for (int off = SP_LANES >> 1; off >= 1; off >>= 1) {
+                top.merge_xor(off, todo);
+                u64 o = __shfl_xor_sync(FULLM, hzl, off);
+                hzl = o < hzl ? o : hzl;
+            }
+            if (todo) {
+                u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
+                u64 bound = top.at(R - 1);
+                if (gg == ~0ull || bound < gg) {
+                    todo = false;
+                    if (sub == 0) write_result<S, FILT_NONE, W>(a, q, top, hzl < gg ? hzl : gg);
+                }
+            }
+            L++;
+        }
+    }
+}
+
 // One warp per aligned chunk of 32 Morton positions: the least live key primary.
 __global__ void chunk_min_kernel(const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
                                  int64_t n, u64* cmin) {
@@ -680,6 +787,33 @@ cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, 
     b.glist = glist;
     b.gcount = gcount;
     return launch_knn(g, b, st);
+}
+
+template <int S>
+static cudaError_t launch_sparse_s(const GridView& g, const KnnArgs& a, const int* list,
+                                   const int* count, int64_t cap, cudaStream_t st) {
+    int64_t warps = (cap + 32 / SP_LANES - 1) / (32 / SP_LANES);
+    int64_t blocks = (warps + PD_WARPS - 1) / PD_WARPS;
+    int64_t lim = (int64_t)device_sms() * 12;
+    if (blocks > lim) blocks = lim;
+    if (blocks < 1) blocks = 1;
+    if (a.term != 0)
+        knn_sparse_kernel<S, true><<<(unsigned)blocks, PD_WARPS * 32, 0, st>>>(g, a, list, count);
+    else
+        knn_sparse_kernel<S, false><<<(unsigned)blocks, PD_WARPS * 32, 0, st>>>(g, a, list, count);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_sparse(const GridView& g, const KnnArgs& a, const int* list,
+                              const int* count, int64_t cap, cudaStream_t st) {
+    if (a.filter != FILT_NONE || cap <= 0) return cap <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+    switch (a.S) {
+        case 4: return launch_sparse_s<4>(g, a, list, count, cap, st);
+        case 8: return launch_sparse_s<8>(g, a, list, count, cap, st);
+        case 17: return launch_sparse_s<17>(g, a, list, count, cap, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st) {

@@ -138,6 +138,11 @@ cudaError_t launch_chunk_min(const u64* prim, const uint8_t* alive, int64_t n, u
 cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, int* gcount,
                                cudaStream_t st);
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
+// Full (FILT_NONE) searches of the listed Morton positions list[0 .. *count)
+// (count on the device, at most cap), 4 lanes per query, each over its own
+// leaf cells: for sparse re-searches.
+cudaError_t launch_knn_sparse(const GridView& g, const KnnArgs& a, const int* list,
+                              const int* count, int64_t cap, cudaStream_t st);
 // Internal neighbour-weight term: unit weights with equal distances ordered by
 // input index (the normals' 16-NN order).
 #define PD_TERM_INDEX_TIE 3
