@@ -54,10 +54,14 @@ WORKLOADS = {
                  gen=lambda seed: synth.site_scan(seed=seed, stations=40, rgb=True),
                  sample_gen=lambda seed: synth.site_scan(seed=seed, stations=40,
                                                          station_ids=[0], rgb=False),
-                 k=1, ratio=0.05, sample=400_000, ref_sample=150_000),
+                 k=1, ratio=0.05, sample=400_000, ref_sample=150_000, tune_sample=25_000_000),
     "site4": dict(desc="merged site scan, 4 stations x 10000x2500 rays (100M points) of the "
                        "200x200x30 m site generator, int32 mm; k=1; keep 5%",
                   gen=lambda seed: synth.site_scan(seed=seed, station_ids=[0, 1, 2, 3], rgb=False),
+                  k=1, ratio=0.05, sample=400_000, ref_sample=150_000),
+    "site1": dict(desc="one station of the site generator, 10000x2500 rays (25M points), int32 "
+                       "mm; k=1; keep 5% (profiling case)",
+                  gen=lambda seed: synth.site_scan(seed=seed, station_ids=[0], rgb=False),
                   k=1, ratio=0.05, sample=400_000, ref_sample=150_000),
     "outdoor": dict(desc="outdoor single-station scan, 10000x2000 rays, 15% dropout, "
                          "ground + 40 boxes + 20 spheres at 1-60 m, int32 mm; k=4; keep 10%",
@@ -499,10 +503,10 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         print(json.dumps({"knn_only": True, "n": n, "k": k}))
         return
 
-    # leaf capacity: autotuned once on a 2M-point sample (outside the timed
-    # region), unless given
-    leaf = args.leaf_max or pd.pd_autotune(ctx, xyz_dev, wl["ratio"], k=k, sample=2_000_000,
-                                           stream=stream)
+    # leaf capacity: autotuned once on a sample (the first 2M points, or the
+    # workload's own sample size; outside the timed region), unless given
+    leaf = args.leaf_max or pd.pd_autotune(ctx, xyz_dev, wl["ratio"], k=k,
+                                           sample=wl.get("tune_sample", 2_000_000), stream=stream)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -541,11 +545,15 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
         pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)   # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        # the host-buffer leg repeats the same step; at most 5 of them keep a
+        # billion-point run within minutes
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        for _ in range(e2e_steps):
             pd.pd_decimate_host(ctx, xyz_np, m, k=k, keep=keep_np, stream=stream)
-        e2e_s, e2e_units = aggregate(time.perf_counter() - t0, n * args.steps, dist)
+        e2e_s, e2e_units = aggregate(time.perf_counter() - t0, n * e2e_steps, dist)
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * n,
-               "d2h_bytes_per_step": n}
+               "d2h_bytes_per_step": n, "steps": e2e_steps,
+               "timed": "host clock around pd_decimate_host calls (pinned host buffers)"}
 
     roofline = rooflines(stats, n, k, leaf, radix_passes(scan.xyz), step_ms, clk,
                          torch.cuda.current_device())
@@ -595,6 +603,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="site", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="steps of the host-buffer leg (at most --steps)")
     ap.add_argument("--leaf-max", type=int, default=0,
                     help="octree leaf capacity, 4..32 (0: the library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")

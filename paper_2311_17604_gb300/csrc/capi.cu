@@ -133,7 +133,8 @@ struct pd_grid {
     std::vector<void*> owned;
     pd_stats stats;
     double ms_grid;  // device time of the pd_build_grid call
-    int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8)
+    int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8;
+                     //   the rest of the 8 stored are kept below the reported horizon)
     int sparse_rq;   // re-searches over a list of the flagged points, 4 lanes each (else per group)
     int* rq_list;    // during a decimation: flagged Morton positions and their count
     int* rq_count;
@@ -333,7 +334,7 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     g->max_rounds = getenv("PD_MAX_ROUNDS") ? atoi(getenv("PD_MAX_ROUNDS")) : 0;
     // diagnostic: exact depth of the k = 1 searches (any depth gives the same
     // result; the stored list is complete below the reported horizon)
-    g->k1_exact = getenv("PD_K1_EXACT") ? atoi(getenv("PD_K1_EXACT")) : 0;
+    g->k1_exact = getenv("PD_K1_EXACT") ? atoi(getenv("PD_K1_EXACT")) : 2;
     // diagnostic: 0 runs the re-searches per leaf group (same results)
     g->sparse_rq = getenv("PD_SPARSE_REQUERY") ? atoi(getenv("PD_SPARSE_REQUERY")) : 1;
     g->n = n;

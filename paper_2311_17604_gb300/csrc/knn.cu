@@ -609,6 +609,7 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, K
                                                                   const int* __restrict__ list,
                                                                   const int* __restrict__ count) {
     const int lane = threadIdx.x & 31, sub = lane & (SP_LANES - 1);
+    const int lead = lane & ~(SP_LANES - 1);  // first lane of this query's group of 4
     const int nq = *count;
     const int per_warp = 32 / SP_LANES;
     const int wid = blockIdx.x * PD_WARPS + (threadIdx.x >> 5);
@@ -628,64 +629,98 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, K
         }
         const int ux = qp.x - g.origin.x, uy = qp.y - g.origin.y, uz = qp.z - g.origin.z;
         while (__any_sync(FULLM, todo)) {
+            int cx = 0, cy = 0, cz = 0;
+            if (L < g.B) {
+                cx = (int)compact3(c0 >> (3 * L));
+                cy = (int)compact3(c0 >> (3 * L + 1));
+                cz = (int)compact3(c0 >> (3 * L + 2));
+            }
+            // resolve the 27 cells, the 4 lanes of a query taking every 4th one
+            uint32_t rb[7], re[7];
+            int rt[7], rl[7];
+#pragma unroll
+            for (int u = 0; u < 7; u++) {
+                int r = 4 * u + sub;
+                rt[u] = 0;
+                rb[u] = re[u] = 0;
+                rl[u] = L;
+                if (todo && r < 27) {
+                    int o = kCellOrder[r];
+                    rt[u] = resolve_cell(g, L, cx + o % 3 - 1, cy + (o / 3) % 3 - 1, cz + o / 9 - 1,
+                                         rb[u], re[u], &rl[u]);
+                }
+            }
             TopList<S, W> top;
             top.init();
             u64 hzl = ~0ull;
-            int cx = 0, cy = 0, cz = 0;
-            if (todo) {
-                if (L < g.B) {
-                    cx = (int)compact3(c0 >> (3 * L));
-                    cy = (int)compact3(c0 >> (3 * L + 1));
-                    cz = (int)compact3(c0 >> (3 * L + 2));
+            const int lim = L <= g.B ? 1 << (g.B - L) : 1;  // L passes B only on finished lanes
+            for (int r = 0; r < 27; r++) {  // warp-uniform: every lane takes part in the shuffles
+                const int u = r >> 2, src = lead + (r & 3);
+                int t_ = 0, l_ = L;
+                uint32_t b_ = 0, e_ = 0;
+#pragma unroll
+                for (int v = 0; v < 7; v++)
+                    if (v == u) {
+                        t_ = rt[v];
+                        l_ = rl[v];
+                        b_ = rb[v];
+                        e_ = re[v];
+                    }
+                const int tr = __shfl_sync(FULLM, t_, src);
+                const int lv = __shfl_sync(FULLM, l_, src);
+                const uint32_t b = __shfl_sync(FULLM, b_, src), e = __shfl_sync(FULLM, e_, src);
+                if (!todo || !tr) continue;
+                const int o = kCellOrder[r];
+                const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                const int sh = lv - L;
+                if (tr == 2) {
+                    // a coarse leaf covers every cell whose coordinates agree with this
+                    // one's above its level: scan it from the first such cell only
+                    bool dup = false;
+                    for (int r2 = 0; r2 < r && !dup; r2++) {
+                        int o2 = kCellOrder[r2];
+                        int ex = cx + o2 % 3 - 1, ey = cy + (o2 / 3) % 3 - 1, ez = cz + o2 / 9 - 1;
+                        if (ex < 0 || ey < 0 || ez < 0 || ex >= lim || ey >= lim || ez >= lim) continue;
+                        dup = (ex >> sh) == ((cx + dx) >> sh) && (ey >> sh) == ((cy + dy) >> sh) &&
+                              (ez >> sh) == ((cz + dz) >> sh);
+                    }
+                    if (dup) continue;
                 }
-                const int lim = 1 << (g.B - L);
-                for (int r = 0; r < 27; r++) {
-                    int o = kCellOrder[r];
-                    int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                    uint32_t b, e;
-                    int rl = L;
-                    int rt = resolve_cell(g, L, cx + dx, cy + dy, cz + dz, b, e, &rl);
-                    if (!rt) continue;
-                    if (rt == 2) {
-                        // a coarse leaf covers every cell whose coordinates agree with
-                        // this one's above level rl: scan it from the first such cell only
-                        const int sh = rl - L;
-                        bool dup = false;
-                        for (int r2 = 0; r2 < r && !dup; r2++) {
-                            int o2 = kCellOrder[r2];
-                            int ex = cx + o2 % 3 - 1, ey = cy + (o2 / 3) % 3 - 1, ez = cz + o2 / 9 - 1;
-                            if (ex < 0 || ey < 0 || ez < 0 || ex >= lim || ey >= lim || ez >= lim)
-                                continue;
-                            dup = (ex >> sh) == ((cx + dx) >> sh) && (ey >> sh) == ((cy + dy) >> sh) &&
-                                  (ez >> sh) == ((cz + dz) >> sh);
-                        }
-                        if (dup) continue;
+                u64 bd = box_d2(ux, uy, uz, (cx + dx) >> sh, (cy + dy) >> sh, (cz + dz) >> sh,
+                                lv + g.shift);
+                u64 bound = top.at(R - 1);
+                if (bound != ~0ull && bd > bound) {
+                    if (bd < hzl) hzl = bd;
+                    continue;
+                }
+                // 4 candidates per lane and step, their loads issued together
+                for (uint32_t j0 = b + sub; j0 < e; j0 += 4 * SP_LANES) {
+                    int4 v4[4];
+                    bool ok[4];
+#pragma unroll
+                    for (int w = 0; w < 4; w++) {
+                        uint32_t j = j0 + (uint32_t)(w * SP_LANES);
+                        ok[w] = j < e && (int)j != q;
+                        v4[w] = ok[w] ? g.pos[j] : make_int4(0, 0, 0, 0);
+                        if (ok[w] && a.alive) ok[w] = a.alive[j] != 0;
                     }
-                    int bxr = (cx + dx) >> (rl - L), byr = (cy + dy) >> (rl - L),
-                        bzr = (cz + dz) >> (rl - L);
-                    u64 bd = box_d2(ux, uy, uz, bxr, byr, bzr, rl + g.shift);
-                    u64 bound = top.at(R - 1);
-                    if (bound != ~0ull && bd > bound) {
-                        if (bd < hzl) hzl = bd;
-                        continue;
-                    }
-                    for (uint32_t j = b + sub; j < e; j += SP_LANES) {
-                        if ((int)j == q) continue;
-                        if (a.alive && !a.alive[j]) continue;
-                        int4 v = g.pos[j];
-                        long long ddx = (long long)v.x - qp.x, ddy = (long long)v.y - qp.y,
-                                  ddz = (long long)v.z - qp.z;
+#pragma unroll
+                    for (int w = 0; w < 4; w++) {
+                        if (!ok[w]) continue;
+                        const int j = (int)(j0 + (uint32_t)(w * SP_LANES));
+                        long long ddx = (long long)v4[w].x - qp.x, ddy = (long long)v4[w].y - qp.y,
+                                  ddz = (long long)v4[w].z - qp.z;
                         u64 dd = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
-                        int co = W ? v.w : (int)j;
-                        if (top.beats_last(dd, (int)j, co)) top.insert(dd, (int)j, co);
+                        int co = W ? v4[w].w : j;
+                        if (top.beats_last(dd, j, co)) top.insert(dd, j, co);
                     }
                 }
             }
             // merge the 4 partial lists and horizons of each query (all lanes take part)
             for (int off = SP_LANES >> 1; off >= 1; off >>= 1) {
                 top.merge_xor(off, todo);
-                u64 o = __shfl_xor_sync(FULLM, hzl, off);
-                hzl = o < hzl ? o : hzl;
+                u64 ho = __shfl_xor_sync(FULLM, hzl, off);
+                hzl = ho < hzl ? ho : hzl;
             }
             if (todo) {
                 u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);

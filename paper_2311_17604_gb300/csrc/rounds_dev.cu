@@ -201,8 +201,10 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n || !alive[s]) return;
     u64 ps = prim[s];
+    const u64 tp = rd->tau_prim;
+    if (ps < tp) return;  // below the threshold on the primary: no index needed
     int is = pos[s].w;
-    if (key_gt(rd->tau_prim, rd->tau_idx, ps, is)) return;
+    if (key_gt(tp, rd->tau_idx, ps, is)) return;
     uint8_t fl = flg[s];
     if (fl & 2) {
         slow[atomicAdd(&rd->nslow, 1)] = (int)s;
@@ -386,7 +388,14 @@ __global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
     bool upd = false, req = false;
     if (s < n) {
         uint8_t dv = 0;
+        // only a removed shell member changes the key or the shell; removed
+        // entries past the shell stay stored (stale) until the shell changes
+        bool shell_hit = false;
         if (alive[s]) {
+            int shell = b.flg[s] >> 2;
+            for (int i = 0; i < shell && !shell_hit; i++) shell_hit = !alive[b.nbr[s * S + i]];
+        }
+        if (shell_hit) {
             int ids[K1_SMAX];
             int r = 0;
             bool dead = false;

@@ -92,3 +92,23 @@ def test_weighted_terms_within_tolerance(pd, ctx, term, k):
     assert int(keep.sum()) == m
     agree = float((keep == ref_keep).mean())
     assert agree >= 0.999, agree
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_colour_batch_equals_alone(pd, ctx, k):
+    """The batched workload's cost (density + 0.3 x colour term): every scan of
+    a batch gets exactly the retained set it gets alone (the term's tolerance
+    against the oracle is checked in test_weighted_terms_within_tolerance)."""
+    scans = _scans()
+    clouds = [{"xyz": torch.from_numpy(s.xyz).cuda(), "rgb": torch.from_numpy(s.rgb).cuda(),
+               "ratio": r} for s, r in scans]
+    kw = dict(k=k, term=pd.PD_TERM_COLOR, weight=0.3)
+    keeps, stats = pd.pd_decimate_batch(ctx, clouds, concurrency=3, **kw)
+    for (s, r), c, keep in zip(scans, clouds, keeps):
+        m = oracle.target_count(s.n, r)
+        got = keep.cpu().numpy()
+        assert int(got.sum()) == m
+        g = pd.Grid(ctx, c["xyz"], rgb=c["rgb"])
+        alone = pd.pd_decimate_count(g, m, **kw).cpu().numpy()
+        g.free()
+        assert np.array_equal(got, alone)
