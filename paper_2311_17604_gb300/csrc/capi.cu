@@ -1039,6 +1039,13 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             }
             h.live -= removed;
             h.removed = (unsigned long long)removed;
+            if (!g->density_k1) {
+                // an overflowing round always narrows the band, as before
+                h.band = host_next_band(h.band, h.band_max, h.band_mode,
+                                        h.cap_over + (h.overflow ? 1 : 0), h.ncand, h.removed);
+                CK(cudaMemcpyAsync(&rd->band, &h.band, sizeof(h.band), cudaMemcpyHostToDevice,
+                                   g->st));
+            }
             CK(cudaMemcpyAsync(&rd->live, &h.live, sizeof(h.live), cudaMemcpyHostToDevice,
                                g->st));
             CK(cudaMemcpyAsync(&rd->tot_requery, &h.tot_requery, sizeof(u64),

@@ -158,6 +158,11 @@ struct SelectResult {
 namespace pd {
 // ---------------------------------------------------------------- rounds_dev.cu
 cudaError_t round_launch_setup(RoundDev* rd, cudaStream_t st);
+// The candidate band of the next round (k >= 2 and weighted costs) from this
+// round's counts; the same arithmetic runs on the device after a normal round
+// and on the host after a round it settled.
+double host_next_band(double band, double band_max, int band_mode, unsigned long long cap_over,
+                      long long ncand, unsigned long long removed);
 cudaError_t round_launch_finish(RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
                                 SelBuffers& b, RoundDev* rd, cudaStream_t st);

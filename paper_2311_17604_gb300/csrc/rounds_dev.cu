@@ -40,23 +40,38 @@ __global__ void round_setup_kernel(RoundDev* rd) {
     for (int i = 0; i < PD_FIX_ITERS; i++) rd->changed[i] = 0;
 }
 
+__device__ __host__ inline double next_band(double band, double band_max, int band_mode,
+                                            unsigned long long cap_over, long long ncand,
+                                            unsigned long long removed) {
+    bool shrink = cap_over != 0;
+    double grow = 1.5;
+    if (band_mode == 1) {
+        double yield = ncand > 0 ? (double)removed / ncand : 1.0;
+        shrink = shrink || yield < 0.5;
+        grow = yield > 0.8 ? 1.25 : 1.0;
+    }
+    double b = shrink ? band * 0.5 : band * grow;
+    if (b > band_max) b = band_max;
+    if (b < 1e-7) b = 1e-7;
+    return b;
+}
+
 __global__ void round_finish_kernel(RoundDev* rd) {
     if (threadIdx.x != 0) return;
     rd->live -= (long long)rd->removed;
     rd->tot_sources += (unsigned long long)rd->nsrc;
-    if (!rd->density_k1) {
-        bool shrink = rd->cap_over != 0;
-        double grow = 1.5;
-        if (rd->band_mode == 1) {
-            double yield = rd->ncand > 0 ? (double)rd->removed / rd->ncand : 1.0;
-            shrink = shrink || yield < 0.5;
-            grow = yield > 0.8 ? 1.25 : 1.0;
-        }
-        double b = shrink ? rd->band * 0.5 : rd->band * grow;
-        if (b > rd->band_max) b = rd->band_max;
-        if (b < 1e-7) b = 1e-7;
-        rd->band = b;
+    // a held round (settled on the host) updates its band there, from the
+    // points it finally removes: the band must not depend on whether the
+    // device fixpoint happened to converge within its sweeps
+    if (!rd->density_k1 && !(rd->overflow || rd->fix_unconverged)) {
+        rd->band = next_band(rd->band, rd->band_max, rd->band_mode, rd->cap_over, rd->ncand,
+                             rd->removed);
     }
+}
+
+double host_next_band(double band, double band_max, int band_mode, unsigned long long cap_over,
+                      long long ncand, unsigned long long removed) {
+    return next_band(band, band_max, band_mode, cap_over, ncand, removed);
 }
 
 // ------------------------------------------------------------------ selection
