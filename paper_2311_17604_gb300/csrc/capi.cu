@@ -138,6 +138,8 @@ struct pd_grid {
     int sparse_rq;   // re-searches over a list of the flagged points, 4 lanes each (else per group)
     int* rq_list;    // during a decimation: flagged Morton positions and their count
     int* rq_count;
+    char* arena;     // during a decimation: scratch of the per-round compactions
+    size_t arena_cap;
     int trace;       // PD_TRACE set: one line per removal round on stderr
     int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
 };
@@ -157,6 +159,34 @@ Scratch scratch_of(pd_grid* g) {
     s.alloc = scratch_alloc;
     s.free = scratch_free;
     s.self = g;
+    return s;
+}
+
+// Bump allocation from the grid's round arena (no allocator call per round:
+// the batch runs many small decimations from several host threads).  The
+// blocks of one compaction are released together by resetting the arena.
+struct ArenaUse {
+    pd_grid* g;
+    size_t used;
+};
+void* arena_alloc(void* self, size_t bytes) {
+    ArenaUse* a = (ArenaUse*)self;
+    size_t b = (bytes + 255) & ~(size_t)255;
+    if (!a->g->arena || a->used + b > a->g->arena_cap) return nullptr;
+    void* p = a->g->arena + a->used;
+    a->used += b;
+    return p;
+}
+void arena_free(void*, void*) {}
+// Scratch over the round arena when the decimation has one, else the allocator.
+Scratch round_scratch(pd_grid* g, ArenaUse* a) {
+    if (!g->arena) return scratch_of(g);
+    a->g = g;
+    a->used = 0;
+    Scratch s;
+    s.alloc = arena_alloc;
+    s.free = arena_free;
+    s.self = a;
     return s;
 }
 
@@ -718,7 +748,8 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
     if (filter == FILT_BELOW_TAU) a.lam_out = fout;
     if (filter == FILT_NONE && g->sparse_rq && g->rq_list) {
         // re-searches: the flagged points, listed, 4 lanes each over their own cells
-        CK(stable_compact(qflag, g->ng, g->rq_list, g->rq_count, scratch_of(g), g->st));
+        ArenaUse au;
+        CK(stable_compact(qflag, g->ng, g->rq_list, g->rq_count, round_scratch(g, &au), g->st));
         CK(launch_knn_sparse(view_of(g), a, g->rq_list, g->rq_count, g->ng, g->st));
         return PD_OK;
     }
@@ -816,6 +847,8 @@ struct RoundScratch {
         g->cmin = nullptr;
         g->rq_list = nullptr;  // released with ptrs
         g->rq_count = nullptr;
+        g->arena = nullptr;
+        g->arena_cap = 0;
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     }
@@ -907,6 +940,14 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         RALLOC(g->rq_list, int, cap);
         RALLOC(g->rq_count, int, 1);
     }
+    {
+        // offsets of one compaction (a word per 1024 points) and the sums of
+        // its scan (a word per 1024 offsets, recursively), 256-byte aligned
+        size_t nb = (size_t)(cap + 1023) / 1024;
+        size_t words = nb + nb / 512 + 64;
+        g->arena_cap = words * 4 + 8 * 256;
+        RALLOC(g->arena, char, g->arena_cap);
+    }
     RALLOC(cand, int, cap);
     RALLOC(slow, int, cap);
     CK(cudaMemsetAsync(inP, 0, cap, g->st));
@@ -988,7 +1029,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             {
                 Span t(T, &g->stats.ms_danger);
                 // candidates in Morton order, so each source finds its own by search
-                CK(stable_compact(inP, g->ng, csort, &rd->ncs, scratch_of(g), g->st));
+                ArenaUse au;
+                CK(stable_compact(inP, g->ng, csort, &rd->ncs, round_scratch(g, &au), g->st));
                 CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k,
                                        pairs, pair_cap, csort, rd, g->st));
             }
