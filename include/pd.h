@@ -112,6 +112,8 @@ typedef struct {
     int32_t iterations;       /* pd_decimate_wup: cost-update iterations (0 otherwise) */
     double ms_grid;           /* device time of the pd_build_grid call that made the grid */
     int64_t live_rounds;      /* sum over the removal rounds of the live count */
+    int64_t graph_rounds;     /* rounds replayed from a captured CUDA graph (their phases
+                                 are in ms_total only, not in the phase timers) */
 } pd_stats;
 
 /* Context: owns nothing but the allocator hooks, the error string and caches. */

@@ -135,7 +135,8 @@ struct pd_grid {
     double ms_grid;  // device time of the pd_build_grid call
     int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8;
                      //   the rest of the 8 stored are kept below the reported horizon)
-    int sparse_rq;   // re-searches over a list of the flagged points, 4 lanes each (else per group)
+    int sparse_rq;   // k = 1 density re-searches over a list of the flagged points, 4 lanes
+                     //   each (else a warp per flagged leaf group)
     int* rq_list;    // during a decimation: flagged Morton positions and their count
     int* rq_count;
     char* arena;     // during a decimation: scratch of the per-round compactions
@@ -520,6 +521,7 @@ struct Timers {
     };
     std::vector<Span> spans;
     cudaStream_t st;
+    bool off = false;  // set while a round is captured into a graph
     explicit Timers(cudaStream_t s) : st(s) {}
     Span* open(double* acc) {
         Span sp;
@@ -546,8 +548,13 @@ struct Timers {
 };
 struct Span {
     Timers& t;
-    Span(Timers& tt, double* acc) : t(tt) { t.open(acc); }
-    ~Span() { t.close(); }
+    bool on;
+    Span(Timers& tt, double* acc) : t(tt), on(!tt.off) {
+        if (on) t.open(acc);
+    }
+    ~Span() {
+        if (on) t.close();
+    }
 };
 
 // kNN over every grid point (full mode)
@@ -747,7 +754,9 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
     if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
     if (filter == FILT_BELOW_TAU) a.lam_out = fout;
     if (filter == FILT_NONE && g->sparse_rq && g->rq_list) {
-        // re-searches: the flagged points, listed, 4 lanes each over their own cells
+        // k = 1 density re-searches: the flagged points, listed, 4 lanes each
+        // over their own cells (the weighted and k >= 2 rounds re-search few
+        // points per round, where a warp per flagged group measured faster)
         ArenaUse au;
         CK(stable_compact(qflag, g->ng, g->rq_list, g->rq_count, round_scratch(g, &au), g->st));
         CK(launch_knn_sparse(view_of(g), a, g->rq_list, g->rq_count, g->ng, g->st));
@@ -840,8 +849,22 @@ struct RoundScratch {
     pd_grid* g;
     std::vector<void*> ptrs;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // replayed rounds: the instantiated graph, its stream and fork/join events
+    cudaGraphExec_t gx = nullptr;
+    cudaStream_t gs = nullptr;
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;
+    cudaEvent_t tq0 = nullptr, tq1 = nullptr;  // trace only: a round's re-search time
     explicit RoundScratch(pd_grid* gg) : g(gg) {}
     ~RoundScratch() {
+        if (tq0) cudaEventDestroy(tq0);
+        if (tq1) cudaEventDestroy(tq1);
+        if (gx) cudaGraphExecDestroy(gx);
+        if (gs) {
+            cudaStreamSynchronize(gs);
+            cudaStreamDestroy(gs);
+        }
+        if (gfork) cudaEventDestroy(gfork);
+        if (gjoin) cudaEventDestroy(gjoin);
         for (void* p : ptrs) gfree(g, p);
         gfree(g, g->cmin);
         g->cmin = nullptr;
@@ -858,6 +881,20 @@ struct RoundScratch {
         ALLOC(ptr, type, count);              \
         rs.ptrs.push_back((void*)(ptr));      \
     } while (0)
+
+// kernel nodes of a captured graph (launch accounting of replayed rounds)
+long long count_kernel_nodes(cudaGraph_t graph) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return 0;
+    long long c = 0;
+    for (size_t i = 0; i < nn; i++) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) c++;
+    }
+    return c;
+}
 
 int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep_dev) {
     int rc = check_cost(g, cp);
@@ -936,7 +973,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     RALLOC(inP, uint8_t, cap);
     RALLOC(rej, uint8_t, cap);
     RALLOC(dirty, uint8_t, cap);
-    if (g->sparse_rq) {
+    if (g->sparse_rq && g->density_k1) {
         RALLOC(g->rq_list, int, cap);
         RALLOC(g->rq_count, int, 1);
     }
@@ -989,6 +1026,75 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     h.band_mode = getenv("PD_BAND_MODE") ? atoi(getenv("PD_BAND_MODE")) : 1;
     CK(cudaMemcpyAsync(rd, &h, sizeof(h), cudaMemcpyHostToDevice, g->st));
     int64_t built = live;
+    // small clouds are bound by launches: from the third round on, a round's
+    // launches are captured into a CUDA graph and replayed (PD_ROUND_GRAPH:
+    // 1 always, 0 never; default for grids up to 8M points)
+    bool round_graph = g->n <= ((int64_t)8 << 20);
+    if (getenv("PD_ROUND_GRAPH")) round_graph = atoi(getenv("PD_ROUND_GRAPH")) != 0;
+    void* graph_pos = nullptr;
+    long long graph_kernels = 0;
+    if (g->trace) {
+        cudaEventCreate(&rs.tq0);
+        cudaEventCreate(&rs.tq1);
+    }
+    cudaEvent_t tq0 = rs.tq0, tq1 = rs.tq1;
+    auto issue_round = [&]() -> int {
+            GridView v = view_of(g);
+            CK(round_launch_setup(rd, g->st));
+            {
+                Span t(T, &g->stats.ms_select);
+                CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+            }
+            if (g->density_k1) {
+                CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
+                                   rej, cand, slow, g->st));
+            } else {
+                BufView bv = bufview(g, cp);
+                CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,
+                                         g->st));
+                CK(launch_chunk_min(g->prim, g->alive, g->ng, g->cmin, g->st));
+                {
+                    Span t(T, &g->stats.ms_knn);
+                    rc = knn_flag(g, cp, FILT_BELOW_SELF, Sf, fqf, fprim, rd);
+                    if (rc) return rc;
+                }
+                CK(round_launch_kk_accept(fqf, g->prim, fprim, g->ng, rd, inP, cand, g->st));
+                {
+                    Span t(T, &g->stats.ms_knn);
+                    rc = knn_flag(g, cp, FILT_BELOW_TAU, Sf, dgf, lam, rd);
+                    if (rc) return rc;
+                }
+                {
+                    Span t(T, &g->stats.ms_danger);
+                    // candidates in Morton order, so each source finds its own by search
+                    ArenaUse au;
+                    CK(stable_compact(inP, g->ng, csort, &rd->ncs, round_scratch(g, &au), g->st));
+                    CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k,
+                                           pairs, pair_cap, csort, rd, g->st));
+                }
+                CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
+            }
+            CK(round_launch_remove(cand, inP, rej, g->alive, rd, g->st));
+            if (g->density_k1) {
+                // absorb removals in the stored 8 nearest; search where the new
+                // nearest shell may be incomplete
+                CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
+            } else if (use_buf) {
+                // absorb removals in the k+b buffers; search only where < k remain
+                CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
+            } else {
+                CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
+            }
+            if (g->trace) cudaEventRecord(tq0, g->st);
+            {
+                Span t(T, &g->stats.ms_knn_requery);
+                rc = knn_flag(g, cp, FILT_NONE, S, dirty, nullptr, rd);
+                if (rc) return rc;
+            }
+            if (g->trace) cudaEventRecord(tq1, g->st);
+            CK(round_launch_finish(rd, g->st));
+            return PD_OK;
+    };
     while (live > m) {
         g->stats.rounds++;
         g->stats.live_rounds += live;
@@ -1001,65 +1107,54 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             set_err(g->ctx, "pd_decimate: round limit reached%s (live = %lld)", "", live);
             return PD_EINTERNAL;
         }
-        GridView v = view_of(g);
-        CK(round_launch_setup(rd, g->st));
-        {
-            Span t(T, &g->stats.ms_select);
-            CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+        int rr = PD_OK;
+        const bool replay = round_graph && g->stats.rounds >= 3 && !g->trace;
+        if (replay && (!rs.gx || graph_pos != (void*)g->pos)) {
+            // capture this round's launches once per grid layout (compaction
+            // replaces the arrays) on a private stream, then replay the graph
+            if (rs.gx) {
+                cudaGraphExecDestroy(rs.gx);
+                rs.gx = nullptr;
+            }
+            if (!rs.gs) {
+                cudaStreamCreateWithFlags(&rs.gs, cudaStreamNonBlocking);
+                cudaEventCreateWithFlags(&rs.gfork, cudaEventDisableTiming);
+                cudaEventCreateWithFlags(&rs.gjoin, cudaEventDisableTiming);
+            }
+            cudaStream_t caller = g->st;
+            g->st = rs.gs;
+            T.off = true;
+            cudaGraph_t graph = nullptr;
+            cudaError_t eb = cudaStreamBeginCapture(rs.gs, cudaStreamCaptureModeThreadLocal);
+            int rc_cap = eb ? PD_ECUDA : issue_round();
+            cudaError_t ee = eb ? cudaSuccess : cudaStreamEndCapture(rs.gs, &graph);
+            g->st = caller;
+            T.off = false;
+            if (!eb && !rc_cap && !ee && graph &&
+                cudaGraphInstantiate(&rs.gx, graph, 0) == cudaSuccess) {
+                graph_pos = (void*)g->pos;
+                // the captured launches ran nothing; each replay runs its kernel nodes
+                graph_kernels = count_kernel_nodes(graph);
+                __atomic_fetch_sub(&g_launch_count, graph_kernels, __ATOMIC_RELAXED);
+            } else {
+                rs.gx = nullptr;
+                round_graph = false;  // capture refused: launch the rounds directly
+                cudaGetLastError();
+            }
+            if (graph) cudaGraphDestroy(graph);
         }
-        if (g->density_k1) {
-            CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
-                               rej, cand, slow, g->st));
+        if (replay && rs.gx) {
+            CK(cudaEventRecord(rs.gfork, g->st));
+            CK(cudaStreamWaitEvent(rs.gs, rs.gfork, 0));
+            CK(cudaGraphLaunch(rs.gx, rs.gs));
+            CK(cudaEventRecord(rs.gjoin, rs.gs));
+            CK(cudaStreamWaitEvent(g->st, rs.gjoin, 0));
+            g->stats.graph_rounds++;
+            __atomic_fetch_add(&g_launch_count, graph_kernels, __ATOMIC_RELAXED);
         } else {
-            BufView bv = bufview(g, cp);
-            CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,
-                                     g->st));
-            CK(launch_chunk_min(g->prim, g->alive, g->ng, g->cmin, g->st));
-            {
-                Span t(T, &g->stats.ms_knn);
-                rc = knn_flag(g, cp, FILT_BELOW_SELF, Sf, fqf, fprim, rd);
-                if (rc) return rc;
-            }
-            CK(round_launch_kk_accept(fqf, g->prim, fprim, g->ng, rd, inP, cand, g->st));
-            {
-                Span t(T, &g->stats.ms_knn);
-                rc = knn_flag(g, cp, FILT_BELOW_TAU, Sf, dgf, lam, rd);
-                if (rc) return rc;
-            }
-            {
-                Span t(T, &g->stats.ms_danger);
-                // candidates in Morton order, so each source finds its own by search
-                ArenaUse au;
-                CK(stable_compact(inP, g->ng, csort, &rd->ncs, round_scratch(g, &au), g->st));
-                CK(round_launch_danger(v, src, g->prim, g->alive, inP, rej, lam, g->nbr, S, k,
-                                       pairs, pair_cap, csort, rd, g->st));
-            }
-            CK(round_launch_pairs_fix(pairs, pair_cap, inP, rej, rd, g->st));
+            rr = issue_round();
+            if (rr) return rr;
         }
-        CK(round_launch_remove(cand, inP, rej, g->alive, rd, g->st));
-        if (g->density_k1) {
-            // absorb removals in the stored 8 nearest; search where the new
-            // nearest shell may be incomplete
-            CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
-        } else if (use_buf) {
-            // absorb removals in the k+b buffers; search only where < k remain
-            CK(round_launch_kk_update(bufview(g, cp), g->alive, g->ng, S, k, dirty, rd, g->st));
-        } else {
-            CK(round_launch_dirty(g->alive, g->nbr, g->ng, S, kchk, dirty, rd, g->st));
-        }
-        cudaEvent_t tq0 = nullptr, tq1 = nullptr;  // trace only: this round's re-search time
-        if (g->trace) {
-            cudaEventCreate(&tq0);
-            cudaEventCreate(&tq1);
-            cudaEventRecord(tq0, g->st);
-        }
-        {
-            Span t(T, &g->stats.ms_knn_requery);
-            rc = knn_flag(g, cp, FILT_NONE, S, dirty, nullptr, rd);
-            if (rc) return rc;
-        }
-        if (g->trace) cudaEventRecord(tq1, g->st);
-        CK(round_launch_finish(rd, g->st));
         CK(cudaMemcpyAsync(&h, rd, sizeof(h), cudaMemcpyDeviceToHost, g->st));
         CK(cudaStreamSynchronize(g->st));
         if (h.overflow || h.fix_unconverged) {
@@ -1097,8 +1192,6 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             float rq_ms = 0.f;
             cudaEventSynchronize(tq1);
             cudaEventElapsedTime(&rq_ms, tq0, tq1);
-            cudaEventDestroy(tq0);
-            cudaEventDestroy(tq1);
             fprintf(stderr, "pd round %d live %lld need %lld cand %d removed %llu band %.3g "
                     "sources %d pairs %d cap-over %llu requeries %llu (%.2f ms)%s\n",
                     g->stats.rounds, (long long)live, (long long)(live - m), h.ncand, h.removed,

@@ -74,7 +74,8 @@ class pd_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("ms_select", ctypes.c_double),
                 ("ms_danger", ctypes.c_double), ("pairs_first", ctypes.c_int64),
                 ("leaf_max", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("ms_grid", ctypes.c_double), ("live_rounds", ctypes.c_int64)]
+                ("ms_grid", ctypes.c_double), ("live_rounds", ctypes.c_int64),
+                ("graph_rounds", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
