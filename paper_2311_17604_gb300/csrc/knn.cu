@@ -595,29 +595,109 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_kernel(GridView g, KnnArgs 
 
 // Sparse re-searches: the listed queries (Morton positions, list[0 .. *count))
 // run 8 to a warp, 4 lanes per query, each query over the 3x3x3 cells of its
-// own leaf level.  The 4 lanes resolve the same cells and split every range
-// (lane sub takes positions b + sub, b + sub + 4, ...), each keeping a partial
-// list; the partial lists merge once per level.  A lane skips a range whose
-// box lies beyond its own partial bound (never closer than the merged one),
-// and the smallest box distance it skipped bounds the reported horizon.
-// Used for the re-searches of the removal rounds, where the flagged queries
-// are few per leaf group and a warp per group would idle most lanes.
+// own leaf level.  The 4 lanes of a query resolve its 27 cells (every 4th
+// one) into shared memory; a coarse leaf reached from two cells is kept once.
+// Each lane then walks the staged ranges on its own, taking positions
+// b + sub, b + sub + 4, ... of every range whose box is not beyond its own
+// partial bound (never closer than the merged one; the smallest box distance
+// it skipped bounds the reported horizon), and keeps a partial list; the 4
+// partial lists merge once per level.  Lists are packed (one 64-bit key per
+// entry, 32-bit distances) when every range of the warp's level lies within
+// 3 cells of 2^13 mm.  Used for the re-searches of the removal rounds, where
+// the flagged queries are few per leaf group and a warp per group would idle
+// most lanes.
 #define SP_LANES 4
+#define SP_SLOTS (32 / SP_LANES)
+
+template <int S, bool W, class TL, bool PACK>
+__device__ __forceinline__ void sparse_level(const GridView& g, const KnnArgs& a, int R, int q,
+                                             int4 qp, int ux, int uy, int uz, int L, int cx,
+                                             int cy, int cz, int sub, bool& todo,
+                                             const uint32_t* __restrict__ sb,
+                                             const uint32_t* __restrict__ se,
+                                             const uint8_t* __restrict__ sl) {
+    TL top;
+    top.init();
+    u64 hzl = ~0ull;
+    if (todo) {
+        for (int r = 0; r < 27; r++) {
+            const int lv = sl[r];
+            if (lv == 0xff) continue;
+            const uint32_t b = sb[r], e = se[r];
+            const int o = kCellOrder[r];
+            const int sh = lv - L;
+            const u64 bd = box_d2(ux, uy, uz, (cx + o % 3 - 1) >> sh, (cy + (o / 3) % 3 - 1) >> sh,
+                                  (cz + o / 9 - 1) >> sh, lv + g.shift);
+            const u64 bound = top.at(R - 1);
+            if (bound != ~0ull && bd > bound) {
+                if (bd < hzl) hzl = bd;
+                continue;
+            }
+            // 4 candidates per lane and step, their loads issued together
+            for (uint32_t j0 = b + sub; j0 < e; j0 += 4 * SP_LANES) {
+                int4 v4[4];
+                bool ok[4];
+#pragma unroll
+                for (int w = 0; w < 4; w++) {
+                    const uint32_t j = j0 + (uint32_t)(w * SP_LANES);
+                    ok[w] = j < e && (int)j != q;
+                    v4[w] = ok[w] ? g.pos[j] : make_int4(0, 0, 0, 0);
+                    if (ok[w] && a.alive) ok[w] = a.alive[j] != 0;
+                }
+#pragma unroll
+                for (int w = 0; w < 4; w++) {
+                    if (!ok[w]) continue;
+                    const int j = (int)(j0 + (uint32_t)(w * SP_LANES));
+                    u64 dd;
+                    if (PACK) {
+                        const int dx = v4[w].x - qp.x, dy = v4[w].y - qp.y, dz = v4[w].z - qp.z;
+                        dd = (u64)((uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz));
+                    } else {
+                        const long long dx = (long long)v4[w].x - qp.x,
+                                        dy = (long long)v4[w].y - qp.y,
+                                        dz = (long long)v4[w].z - qp.z;
+                        dd = (u64)(dx * dx + dy * dy + dz * dz);
+                    }
+                    const int co = W ? v4[w].w : j;
+                    if (top.beats_last(dd, j, co)) top.insert(dd, j, co);
+                }
+            }
+        }
+    }
+    // merge the 4 partial lists and horizons of each query (all lanes take part)
+    for (int off = SP_LANES >> 1; off >= 1; off >>= 1) {
+        top.merge_xor(off, todo);
+        const u64 ho = __shfl_xor_sync(FULLM, hzl, off);
+        hzl = ho < hzl ? ho : hzl;
+    }
+    if (todo) {
+        const u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
+        const u64 bound = top.at(R - 1);
+        if (gg == ~0ull || bound < gg) {
+            todo = false;
+            if (sub == 0) write_result<S, FILT_NONE, W>(a, q, top, hzl < gg ? hzl : gg);
+        }
+    }
+}
 
 template <int S, bool W>
 __global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, KnnArgs a,
                                                                   const int* __restrict__ list,
                                                                   const int* __restrict__ count) {
-    const int lane = threadIdx.x & 31, sub = lane & (SP_LANES - 1);
-    const int lead = lane & ~(SP_LANES - 1);  // first lane of this query's group of 4
+    __shared__ uint32_t s_b[PD_WARPS][SP_SLOTS][27], s_e[PD_WARPS][SP_SLOTS][27];
+    __shared__ uint8_t s_l[PD_WARPS][SP_SLOTS][28];
+    const int lane = threadIdx.x & 31, sub = lane & (SP_LANES - 1), slot = lane / SP_LANES;
+    const int w = threadIdx.x >> 5;
+    uint32_t* sb = s_b[w][slot];
+    uint32_t* se = s_e[w][slot];
+    uint8_t* sl = s_l[w][slot];
     const int nq = *count;
-    const int per_warp = 32 / SP_LANES;
-    const int wid = blockIdx.x * PD_WARPS + (threadIdx.x >> 5);
+    const int wid = blockIdx.x * PD_WARPS + w;
     const int nwarps = gridDim.x * PD_WARPS;
     const int R = a.r_exact > 0 && a.r_exact < S ? a.r_exact : S;
-    for (int base = wid * per_warp; base < nq; base += nwarps * per_warp) {  // warp-uniform
-        const int slot = base + lane / SP_LANES;
-        const int q = slot < nq ? list[slot] : -1;
+    for (int base = wid * SP_SLOTS; base < nq; base += nwarps * SP_SLOTS) {  // warp-uniform
+        const int qs = base + slot;
+        const int q = qs < nq ? list[qs] : -1;
         bool todo = q >= 0;
         int4 qp = make_int4(0, 0, 0, 0);
         u64 c0 = 0;
@@ -635,101 +715,49 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, K
                 cy = (int)compact3(c0 >> (3 * L + 1));
                 cz = (int)compact3(c0 >> (3 * L + 2));
             }
-            // resolve the 27 cells, the 4 lanes of a query taking every 4th one
-            uint32_t rb[7], re[7];
-            int rt[7], rl[7];
-#pragma unroll
-            for (int u = 0; u < 7; u++) {
-                int r = 4 * u + sub;
-                rt[u] = 0;
-                rb[u] = re[u] = 0;
-                rl[u] = L;
-                if (todo && r < 27) {
-                    int o = kCellOrder[r];
-                    rt[u] = resolve_cell(g, L, cx + o % 3 - 1, cy + (o / 3) % 3 - 1, cz + o / 9 - 1,
-                                         rb[u], re[u], &rl[u]);
-                }
-            }
-            TopList<S, W> top;
-            top.init();
-            u64 hzl = ~0ull;
-            const int lim = L <= g.B ? 1 << (g.B - L) : 1;  // L passes B only on finished lanes
-            for (int r = 0; r < 27; r++) {  // warp-uniform: every lane takes part in the shuffles
-                const int u = r >> 2, src = lead + (r & 3);
-                int t_ = 0, l_ = L;
-                uint32_t b_ = 0, e_ = 0;
-#pragma unroll
-                for (int v = 0; v < 7; v++)
-                    if (v == u) {
-                        t_ = rt[v];
-                        l_ = rl[v];
-                        b_ = rb[v];
-                        e_ = re[v];
-                    }
-                const int tr = __shfl_sync(FULLM, t_, src);
-                const int lv = __shfl_sync(FULLM, l_, src);
-                const uint32_t b = __shfl_sync(FULLM, b_, src), e = __shfl_sync(FULLM, e_, src);
-                if (!todo || !tr) continue;
-                const int o = kCellOrder[r];
-                const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                const int sh = lv - L;
-                if (tr == 2) {
-                    // a coarse leaf covers every cell whose coordinates agree with this
-                    // one's above its level: scan it from the first such cell only
-                    bool dup = false;
-                    for (int r2 = 0; r2 < r && !dup; r2++) {
-                        int o2 = kCellOrder[r2];
-                        int ex = cx + o2 % 3 - 1, ey = cy + (o2 / 3) % 3 - 1, ez = cz + o2 / 9 - 1;
-                        if (ex < 0 || ey < 0 || ez < 0 || ex >= lim || ey >= lim || ez >= lim) continue;
-                        dup = (ex >> sh) == ((cx + dx) >> sh) && (ey >> sh) == ((cy + dy) >> sh) &&
-                              (ez >> sh) == ((cz + dz) >> sh);
-                    }
-                    if (dup) continue;
-                }
-                u64 bd = box_d2(ux, uy, uz, (cx + dx) >> sh, (cy + dy) >> sh, (cz + dz) >> sh,
-                                lv + g.shift);
-                u64 bound = top.at(R - 1);
-                if (bound != ~0ull && bd > bound) {
-                    if (bd < hzl) hzl = bd;
-                    continue;
-                }
-                // 4 candidates per lane and step, their loads issued together
-                for (uint32_t j0 = b + sub; j0 < e; j0 += 4 * SP_LANES) {
-                    int4 v4[4];
-                    bool ok[4];
-#pragma unroll
-                    for (int w = 0; w < 4; w++) {
-                        uint32_t j = j0 + (uint32_t)(w * SP_LANES);
-                        ok[w] = j < e && (int)j != q;
-                        v4[w] = ok[w] ? g.pos[j] : make_int4(0, 0, 0, 0);
-                        if (ok[w] && a.alive) ok[w] = a.alive[j] != 0;
-                    }
-#pragma unroll
-                    for (int w = 0; w < 4; w++) {
-                        if (!ok[w]) continue;
-                        const int j = (int)(j0 + (uint32_t)(w * SP_LANES));
-                        long long ddx = (long long)v4[w].x - qp.x, ddy = (long long)v4[w].y - qp.y,
-                                  ddz = (long long)v4[w].z - qp.z;
-                        u64 dd = (u64)(ddx * ddx + ddy * ddy + ddz * ddz);
-                        int co = W ? v4[w].w : j;
-                        if (top.beats_last(dd, j, co)) top.insert(dd, j, co);
-                    }
-                }
-            }
-            // merge the 4 partial lists and horizons of each query (all lanes take part)
-            for (int off = SP_LANES >> 1; off >= 1; off >>= 1) {
-                top.merge_xor(off, todo);
-                u64 ho = __shfl_xor_sync(FULLM, hzl, off);
-                hzl = ho < hzl ? ho : hzl;
-            }
+            // resolve the 27 cells into shared memory, the 4 lanes of a query
+            // taking every 4th one
+            bool small = true;  // every range of this lane within 3 cells of 2^13 mm
             if (todo) {
-                u64 gg = L >= g.B ? ~0ull : gap2(g, ux, uy, uz, L, cx, cy, cz);
-                u64 bound = top.at(R - 1);
-                if (gg == ~0ull || bound < gg) {
-                    todo = false;
-                    if (sub == 0) write_result<S, FILT_NONE, W>(a, q, top, hzl < gg ? hzl : gg);
+                const int lim = 1 << (g.B - L);  // todo lanes have L < B or L == B
+                for (int r = sub; r < 27; r += SP_LANES) {
+                    const int o = kCellOrder[r];
+                    const int ex = cx + o % 3 - 1, ey = cy + (o / 3) % 3 - 1, ez = cz + o / 9 - 1;
+                    uint32_t b = 0, e = 0;
+                    int rl = L;
+                    int rt = resolve_cell(g, L, ex, ey, ez, b, e, &rl);
+                    if (rt == 2) {
+                        // a coarse leaf covers every cell that agrees with this one
+                        // above its level: keep it at the first such cell only
+                        const int sh = rl - L;
+                        for (int r2 = 0; r2 < r; r2++) {
+                            const int o2 = kCellOrder[r2];
+                            const int fx = cx + o2 % 3 - 1, fy = cy + (o2 / 3) % 3 - 1,
+                                      fz = cz + o2 / 9 - 1;
+                            if (fx < 0 || fy < 0 || fz < 0 || fx >= lim || fy >= lim || fz >= lim)
+                                continue;
+                            if ((fx >> sh) == (ex >> sh) && (fy >> sh) == (ey >> sh) &&
+                                (fz >> sh) == (ez >> sh)) {
+                                rt = 0;
+                                break;
+                            }
+                        }
+                    }
+                    sb[r] = b;
+                    se[r] = e;
+                    sl[r] = rt ? (uint8_t)rl : (uint8_t)0xff;
+                    if (rt && rl + g.shift > 13) small = false;
                 }
             }
+            const bool pack = __all_sync(FULLM, small);
+            __syncwarp();
+            if (pack)
+                sparse_level<S, W, TopPack<S, W>, true>(g, a, R, q, qp, ux, uy, uz, L, cx, cy, cz,
+                                                        sub, todo, sb, se, sl);
+            else
+                sparse_level<S, W, TopList<S, W>, false>(g, a, R, q, qp, ux, uy, uz, L, cx, cy,
+                                                         cz, sub, todo, sb, se, sl);
+            __syncwarp();
             L++;
         }
     }
