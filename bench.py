@@ -451,6 +451,10 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
     m = oracle.target_count(n, wl["ratio"])
     xyz_dev = torch.from_numpy(scan.xyz).to(dev)
     ctx = pd.Context()
+    if args.device_budget_gb > 0:
+        # clouds beyond device memory: blocks past the budget (and cold ones)
+        # live in pinned host memory that the kernels address in place
+        ctx.set_device_budget(int(args.device_budget_gb * (1 << 30)))
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     L = pd.lib()
@@ -580,7 +584,11 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
             "config": {"workload": wl["desc"], "n": n, "m": m, "k": k, "leaf_max": leaf,
                        "leaf_max_from": "option" if args.leaf_max else "pd_autotune",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "256 MiB buffer written between timed steps; working set > L2"},
+                       "l2": "256 MiB buffer written between timed steps; working set > L2",
+                       **({"device_budget_gb": args.device_budget_gb,
+                           "memory": {key: v for key, v in ctx.memory().items()
+                                      if key in ("device_peak", "host_peak")}}
+                          if args.device_budget_gb > 0 else {})},
             "e2e": e2e,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "batched": batched, "serving": serving,
@@ -607,6 +615,9 @@ def main(argv=None):
                     help="steps of the host-buffer leg (at most --steps)")
     ap.add_argument("--leaf-max", type=int, default=0,
                     help="octree leaf capacity, 4..32 (0: the library default)")
+    ap.add_argument("--device-budget-gb", type=float, default=0.0,
+                    help="device-memory budget of the library's context (GiB); blocks past "
+                         "it live in pinned host memory (0: no budget)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-count", type=int, default=48)

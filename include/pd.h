@@ -119,6 +119,39 @@ typedef struct {
 /* Context: owns nothing but the allocator hooks, the error string and caches. */
 int pd_ctx_create(const pd_allocator* alloc /* may be NULL */, pd_ctx** out);
 void pd_ctx_destroy(pd_ctx* ctx);
+
+/*
+ * Clouds larger than device memory (section "Scaling to massive point
+ * clouds": the paper keeps voxels out of core and pages them in; here the
+ * second tier is the host's memory, which a Grace-Blackwell GPU addresses
+ * directly over NVLink-C2C).  After this call the context tracks its blocks:
+ *   - a block of at least max(1 MiB, spill_min) bytes that would take the
+ *     context's device bytes past `bytes`, and every such block the library
+ *     marks cold (input copies of pd_decimate_host, its keep staging, the
+ *     Morton codes, the k-th distances and horizons), is allocated as pinned,
+ *     mapped host memory (cudaHostAlloc) instead;
+ *   - the kernels address those blocks in place (unified addressing), so a
+ *     decimation gives the same result at any budget, only slower;
+ *   - blocks below 1 MiB (control blocks, counters, histograms: they take
+ *     device atomics) always stay in device memory.
+ * bytes = 0 lifts the budget: nothing more spills (blocks already in host
+ * memory stay there until freed).  Freeing a host block waits for the stream
+ * it was used on.  The budget
+ * counts the context's own allocations only (not the caller's buffers).
+ * Call it between calls, not while another thread uses the context.
+ */
+typedef struct {
+    uint64_t budget;        /* current budget (0: none) */
+    uint64_t device_bytes;  /* tracked device bytes now held */
+    uint64_t device_peak;   /* ... and their peak since the budget was set / reset */
+    uint64_t host_bytes;    /* pinned host bytes now held */
+    uint64_t host_peak;
+    int32_t tracked;        /* 1 once a budget was ever set on this context */
+    int32_t reserved[3];
+} pd_memory;
+int pd_ctx_set_device_budget(pd_ctx* ctx, uint64_t bytes, uint64_t spill_min);
+int pd_ctx_memory(pd_ctx* ctx, pd_memory* out);
+int pd_ctx_reset_peaks(pd_ctx* ctx);
 const char* pd_strerror(int code);
 const char* pd_last_error(const pd_ctx* ctx);
 

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pd.h"
@@ -74,6 +75,14 @@ struct pd_ctx {
     int tuned_leaf;  // leaf capacity chosen by pd_autotune (0: none yet)
     char err[512];
     std::mutex mu;  // guards err (batch slots report errors concurrently)
+    // device-memory budget (0: none).  Under a budget every block is tracked;
+    // large blocks beyond it (and large cold ones) live in pinned host memory
+    // that the kernels address in place.
+    std::mutex mem_mu;
+    std::atomic<bool> tracked{false};  // set once a budget was ever given
+    uint64_t dev_budget = 0, spill_min = 0;
+    uint64_t dev_used = 0, dev_peak = 0, host_used = 0, host_peak = 0;
+    std::unordered_map<void*, std::pair<size_t, bool>> blocks;  // bytes, in host memory
 };
 
 static void set_err(pd_ctx* c, const char* fmt, const char* a = "", long long b = 0) {
@@ -82,9 +91,7 @@ static void set_err(pd_ctx* c, const char* fmt, const char* a = "", long long b 
     snprintf(c->err, sizeof(c->err), fmt, a, b);
 }
 
-static void* ctx_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) {
-    if (bytes == 0) bytes = 16;
-    bytes = (bytes + 255) & ~(size_t)255;
+static void* dev_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) {
     if (c->has_alloc) return c->alloc.alloc(c->alloc.user, bytes, (void*)st);
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
@@ -93,10 +100,84 @@ static void* ctx_alloc(pd_ctx* c, size_t bytes, cudaStream_t st) {
     }
     return p;
 }
-static void ctx_free(pd_ctx* c, void* p, cudaStream_t st) {
-    if (!p) return;
+static void dev_free(pd_ctx* c, void* p, cudaStream_t st) {
     if (c->has_alloc) c->alloc.free(c->alloc.user, p, (void*)st);
     else cudaFreeAsync(p, st);
+}
+
+// Blocks below this size always stay in device memory: the small control
+// blocks, counters and histograms take device atomics.
+#define PD_SPILL_FLOOR ((size_t)1 << 20)
+
+// cold: a block the kernels touch about once (input copies, write-mostly
+// state); under a budget such blocks go to host memory first.
+static void* ctx_alloc(pd_ctx* c, size_t bytes, cudaStream_t st, bool cold = false) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (!c->tracked.load()) return dev_alloc(c, bytes, st);
+    bool host;
+    {
+        std::lock_guard<std::mutex> lk(c->mem_mu);
+        host = c->dev_budget > 0 && bytes >= PD_SPILL_FLOOR && bytes >= c->spill_min &&
+               (cold || c->dev_used + bytes > c->dev_budget);
+        if (!host) c->dev_used += bytes;  // reserved before the call
+    }
+    void* p = nullptr;
+    if (host) {
+        // pinned and mapped: with unified addressing the kernels use the
+        // host address itself (over NVLink-C2C on Grace systems)
+        void* d = nullptr;
+        if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess || d != p) {
+            cudaGetLastError();
+            cudaFreeHost(p);
+            return nullptr;
+        }
+    } else {
+        p = dev_alloc(c, bytes, st);
+    }
+    std::lock_guard<std::mutex> lk(c->mem_mu);
+    if (!p) {
+        if (!host) c->dev_used -= bytes;
+        return nullptr;
+    }
+    if (host) {
+        c->host_used += bytes;
+        c->host_peak = std::max(c->host_peak, c->host_used);
+    } else {
+        c->dev_peak = std::max(c->dev_peak, c->dev_used);
+    }
+    c->blocks[p] = std::make_pair(bytes, host);
+    return p;
+}
+static void ctx_free(pd_ctx* c, void* p, cudaStream_t st) {
+    if (!p) return;
+    if (!c->tracked.load()) {
+        dev_free(c, p, st);
+        return;
+    }
+    bool host = false, known = false;
+    {
+        std::lock_guard<std::mutex> lk(c->mem_mu);
+        auto it = c->blocks.find(p);
+        if (it != c->blocks.end()) {
+            known = true;
+            host = it->second.second;
+            if (host) c->host_used -= it->second.first;
+            else c->dev_used -= it->second.first;
+            c->blocks.erase(it);
+        }
+    }
+    if (known && host) {
+        // not stream-ordered: wait for the work that may still address it
+        cudaStreamSynchronize(st);
+        cudaFreeHost(p);
+    } else {
+        dev_free(c, p, st);
+    }
 }
 
 // ============================================================ grid
@@ -231,6 +312,16 @@ GridView view_of(const pd_grid* g) {
         }                                                                      \
     } while (0)
 
+#define ALLOC_COLD(ptr, type, count)                                                \
+    do {                                                                             \
+        ptr = (type*)ctx_alloc(g->ctx, sizeof(type) * (size_t)(count), g->st, true); \
+        if (!ptr) {                                                                  \
+            set_err(g->ctx, "allocation of %s failed (%lld bytes)", #ptr,            \
+                    (long long)(sizeof(type) * (size_t)(count)));                    \
+            return PD_ENOMEM;                                                        \
+        }                                                                            \
+    } while (0)
+
 void gfree(pd_grid* g, void* p) { ctx_free(g->ctx, p, g->st); }
 
 // Temporary device blocks of one function: released (stream-ordered) when the
@@ -312,6 +403,36 @@ extern "C" int pd_ctx_create(const pd_allocator* alloc, pd_ctx** out) {
 }
 
 extern "C" void pd_ctx_destroy(pd_ctx* ctx) { delete ctx; }
+
+extern "C" int pd_ctx_set_device_budget(pd_ctx* ctx, uint64_t bytes, uint64_t spill_min) {
+    if (!ctx) return PD_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mem_mu);
+    ctx->dev_budget = bytes;
+    ctx->spill_min = spill_min;
+    ctx->tracked.store(true);
+    return PD_OK;
+}
+
+extern "C" int pd_ctx_memory(pd_ctx* ctx, pd_memory* out) {
+    if (!ctx || !out) return PD_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mem_mu);
+    memset(out, 0, sizeof(*out));
+    out->budget = ctx->dev_budget;
+    out->device_bytes = ctx->dev_used;
+    out->device_peak = ctx->dev_peak;
+    out->host_bytes = ctx->host_used;
+    out->host_peak = ctx->host_peak;
+    out->tracked = ctx->tracked.load() ? 1 : 0;
+    return PD_OK;
+}
+
+extern "C" int pd_ctx_reset_peaks(pd_ctx* ctx) {
+    if (!ctx) return PD_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mem_mu);
+    ctx->dev_peak = ctx->dev_used;
+    ctx->host_peak = ctx->host_used;
+    return PD_OK;
+}
 
 extern "C" const char* pd_strerror(int code) {
     switch (code) {
@@ -411,7 +532,7 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
         g->shift = bits > PD_MAXLEVEL ? bits - PD_MAXLEVEL : 0;
         g->B = bits - g->shift;
         if (g->B < 1) g->B = 1;
-        ALLOC(g->code, u64, n);
+        ALLOC_COLD(g->code, u64, n);
         uint32_t* perm;
         Temps tmp(g);
         TALLOC(tmp, perm, uint32_t, n);
@@ -480,9 +601,9 @@ int prepare_state(pd_grid* g, const pd_cost_params* cp) {
     g->density_k1 = dk1;
     if (!g->prim) ALLOC(g->prim, u64, g->n);
     if (!g->nbr) ALLOC(g->nbr, int, (size_t)g->n * S);
-    if (!g->rk2) ALLOC(g->rk2, u64, g->n);
+    if (!g->rk2) ALLOC_COLD(g->rk2, u64, g->n);
     if (!g->flg) ALLOC(g->flg, uint8_t, g->n);
-    if (!g->hz) ALLOC(g->hz, u64, g->n);
+    if (!g->hz) ALLOC_COLD(g->hz, u64, g->n);
     if (cp->term == PD_TERM_ORIENT) {
         if (!g->nrm) ALLOC(g->nrm, float4, g->n);
         // normals are given in input order: gather through pos[].w
@@ -592,7 +713,7 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
     gfree(g, g->pos);
     g->pos = pos2;
     u64* code2;
-    ALLOC(code2, u64, cn);
+    ALLOC_COLD(code2, u64, cn);
     CK(launch_take_u64(list, nl, g->code, code2, g->st));
     gfree(g, g->code);
     g->code = code2;
@@ -617,7 +738,7 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
         gfree(g, g->prim);
         g->prim = p2;
         u64* r2;
-        ALLOC(r2, u64, cn);
+        ALLOC_COLD(r2, u64, cn);
         CK(launch_take_u64(list, nl, g->rk2, r2, g->st));
         gfree(g, g->rk2);
         g->rk2 = r2;
@@ -627,7 +748,7 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
         gfree(g, g->flg);
         g->flg = f2;
         u64* h2;
-        ALLOC(h2, u64, cn);
+        ALLOC_COLD(h2, u64, cn);
         CK(launch_take_u64(list, nl, g->hz, h2, g->st));
         gfree(g, g->hz);
         g->hz = h2;
@@ -776,6 +897,7 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
 // A round the device could not settle: the danger analysis overflowed (or
 // fewer than k low points exist), or the fixpoint needed more sweeps.
 int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint8_t* rej,
+                 int* dep,
                  int* cand, int2* pairs, int pair_cap, int64_t* removed) {
     int* d = g->d_int;
     if (h.overflow) {
@@ -795,7 +917,7 @@ int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint
         for (int it = 0; it < 1000000; it++) {
             CK(cudaMemsetAsync(d + 6, 0, sizeof(int), g->st));
             if (g->density_k1)
-                CK(launch_k1_fix(cand, &rd->ncand, h.ncand, g->pos, g->nbr, g->flg, g->S, inP,
+                CK(launch_k1_fix(dep, &rd->ndep, h.ndep, g->pos, g->nbr, g->flg, g->S, inP,
                                  rej, d + 6, g->st));
             else
                 CK(launch_pair_fix(pairs, &rd->npairs, std::min(h.npairs, pair_cap), pair_cap,
@@ -969,7 +1091,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     int kchk = g->density_k1 ? S : k;
     bool use_buf = !g->density_k1 && S <= 8;
     uint8_t *inP, *rej, *dirty, *fqf = nullptr, *dgf = nullptr;  // dgf: lambda search flags
-    int *cand, *slow, *src = nullptr, *csort = nullptr;
+    int *cand, *slow, *src = nullptr, *csort = nullptr, *dep = nullptr;
     u64 *fprim = nullptr, *lam = nullptr;
     int2* pairs = nullptr;
     int64_t cap = g->n;
@@ -990,6 +1112,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     }
     RALLOC(cand, int, cap);
     RALLOC(slow, int, cap);
+    if (g->density_k1) RALLOC(dep, int, cap);
     CK(cudaMemsetAsync(inP, 0, cap, g->st));
     CK(cudaMemsetAsync(rej, 0, cap, g->st));
     int pair_cap = 0;
@@ -1050,7 +1173,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             }
             if (g->density_k1) {
                 CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
-                                   rej, cand, slow, g->st));
+                                   rej, cand, slow, dep, g->st));
             } else {
                 BufView bv = bufview(g, cp);
                 CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,
@@ -1164,7 +1287,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             // settle on the host: finish the fixpoint, or (danger overflow / too
             // few low points) take only the global maximum, always removable
             int64_t removed = 0;
-            rc = settle_round(g, rd, h, inP, rej, cand, pairs, pair_cap, &removed);
+            rc = settle_round(g, rd, h, inP, rej, dep, cand, pairs, pair_cap, &removed);
             if (rc) return rc;
             if (g->density_k1)
                 CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
@@ -1425,23 +1548,23 @@ extern "C" int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint
                                 int64_t m, uint8_t* keep_host, void* stream, pd_stats* stats) {
     if (!ctx || !xyz_host || !keep_host || !cp || n < 1) return PD_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int32_t* xyz = (int32_t*)ctx_alloc(ctx, (size_t)n * 12, st);
-    uint8_t* rgb = rgb_host ? (uint8_t*)ctx_alloc(ctx, (size_t)n * 3, st) : nullptr;
+    int32_t* xyz = (int32_t*)ctx_alloc(ctx, (size_t)n * 12, st, true);
+    uint8_t* rgb = rgb_host ? (uint8_t*)ctx_alloc(ctx, (size_t)n * 3, st, true) : nullptr;
     float* nrm = normals_host && cp->term == PD_TERM_ORIENT
-                     ? (float*)ctx_alloc(ctx, (size_t)n * 12, st)
+                     ? (float*)ctx_alloc(ctx, (size_t)n * 12, st, true)
                      : nullptr;
-    uint8_t* keep = (uint8_t*)ctx_alloc(ctx, (size_t)n, st);
+    uint8_t* keep = (uint8_t*)ctx_alloc(ctx, (size_t)n, st, true);
     int rc = PD_OK;
     if (!xyz || !keep || (rgb_host && !rgb) || (normals_host && cp->term == PD_TERM_ORIENT && !nrm)) {
         set_err(ctx, "pd_decimate_host: allocation failed%s", "", 0);
         rc = PD_ENOMEM;
     }
     pd_grid* g = nullptr;
-    if (!rc && cudaMemcpyAsync(xyz, xyz_host, (size_t)n * 12, cudaMemcpyHostToDevice, st))
+    if (!rc && cudaMemcpyAsync(xyz, xyz_host, (size_t)n * 12, cudaMemcpyDefault, st))
         rc = PD_ECUDA;
-    if (!rc && rgb && cudaMemcpyAsync(rgb, rgb_host, (size_t)n * 3, cudaMemcpyHostToDevice, st))
+    if (!rc && rgb && cudaMemcpyAsync(rgb, rgb_host, (size_t)n * 3, cudaMemcpyDefault, st))
         rc = PD_ECUDA;
-    if (!rc && nrm && cudaMemcpyAsync(nrm, normals_host, (size_t)n * 12, cudaMemcpyHostToDevice, st))
+    if (!rc && nrm && cudaMemcpyAsync(nrm, normals_host, (size_t)n * 12, cudaMemcpyDefault, st))
         rc = PD_ECUDA;
     if (!rc) rc = pd_build_grid(ctx, xyz, rgb, n, nullptr, stream, &g);
     if (!rc) {
@@ -1450,7 +1573,7 @@ extern "C" int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint
         rc = pd_decimate_count(g, &c2, m, keep, stream);
         if (!rc && stats) pd_grid_stats(g, stats);
     }
-    if (!rc && cudaMemcpyAsync(keep_host, keep, (size_t)n, cudaMemcpyDeviceToHost, st))
+    if (!rc && cudaMemcpyAsync(keep_host, keep, (size_t)n, cudaMemcpyDefault, st))
         rc = PD_ECUDA;
     if (g) pd_grid_free(g);
     ctx_free(ctx, xyz, st);

@@ -208,8 +208,8 @@ cudaError_t radix_sort_pairs(u64* keys, uint32_t* vals, int64_t n, int bits, con
         uint32_t* tv = va; va = vb; vb = tv;
     }
     if (!e && ka != keys) {
-        e = cudaMemcpyAsync(keys, ka, n * sizeof(u64), cudaMemcpyDeviceToDevice, st);
-        if (!e) e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpyAsync(keys, ka, n * sizeof(u64), cudaMemcpyDefault, st);
+        if (!e) e = cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDefault, st);
     }
     s.put(counts);
     s.put(v2);
@@ -294,19 +294,30 @@ cudaError_t launch_leaf_levels(const u64* code, int64_t n, int T, int B, uint8_t
 }
 
 // ------------------------------------------------------------------ cell table
-__device__ inline bool run_head(const u64* code, int64_t i, int L) {
-    return i == 0 || (code[i - 1] >> (3 * L)) != (code[i] >> (3 * L));
+// Highest level at which the level prefixes (code >> 3L) of a and b differ;
+// -1 for equal codes.  Position i opens a level-L cell (a run head) iff
+// i == 0 or L <= diff_level(code[i-1], code[i]); it closes one (a run tail)
+// iff i == n-1 or L <= diff_level(code[i], code[i+1]).
+__device__ inline int diff_level(u64 a, u64 b) {
+    u64 d = a ^ b;
+    return d ? (63 - __clzll((long long)d)) / 3 : -1;
 }
-__device__ inline bool run_tail(const u64* code, int64_t i, int64_t n, int L) {
-    return i == n - 1 || (code[i + 1] >> (3 * L)) != (code[i] >> (3 * L));
+__device__ inline int head_level(const u64* code, int64_t i, int B) {
+    return i == 0 ? B : diff_level(code[i - 1], code[i]);
+}
+__device__ inline int tail_level(const u64* code, int64_t i, int64_t n, int B) {
+    return i == n - 1 ? B : diff_level(code[i], code[i + 1]);
 }
 
+// Octree nodes: one per (level L >= the point's leaf level, run head).
 __global__ void node_count_kernel(const u64* __restrict__ code, const uint8_t* __restrict__ leaf,
                                   int64_t n, int B, unsigned long long* count) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned c = 0;
     if (i < n) {
-        for (int L = leaf[i]; L <= B; L++) c += run_head(code, i, L);
+        int hi = min(head_level(code, i, B), B);
+        int lo = leaf[i];
+        c = hi >= lo ? (unsigned)(hi - lo + 1) : 0u;
     }
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
@@ -334,10 +345,12 @@ __global__ void node_insert_kernel(const u64* __restrict__ code, const uint8_t* 
                                    int64_t n, int B, HashSlot* tab, u64 mask) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int L = leaf[i]; L <= B; L++) {
-        bool h = run_head(code, i, L), t = run_tail(code, i, n, L);
-        if (!h && !t) continue;
-        u64 prefix = code[i] >> (3 * L);
+    const int hh = head_level(code, i, B), ht = tail_level(code, i, n, B);
+    const int top = min(max(hh, ht), B);  // above it i neither opens nor closes a cell
+    const u64 c = code[i];
+    for (int L = leaf[i]; L <= top; L++) {
+        bool h = L <= hh, t = L <= ht;
+        u64 prefix = c >> (3 * L);
         long long slot = hash_insert(tab, mask, cell_key(prefix, L, B));
         if (slot < 0) continue;  // table sized at 2x the node count: cannot fill
         if (h) tab[slot].b = (uint32_t)i;
@@ -360,15 +373,35 @@ __device__ inline bool leaf_range(const GridView& g, int64_t s, uint32_t& b, uin
     return hash_find(g.hash, g.hmask, cell_key(g.code[s] >> (3 * L), L, g.B), b, e);
 }
 
+// Groups of <= 32 consecutive points of one leaf.  Position s starts a group
+// when it opens its leaf, or when the leaf holds 32 or more points before s
+// (leaves above 32 points only occur at level 0) and s - b is a multiple of
+// 32, b the leaf's first position (from the cell table).
 __global__ void leaf_groups_kernel(GridView g, int64_t n, int4* groups, int* ngroups) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    uint32_t b, e;
-    if (!leaf_range(g, s, b, e)) return;
-    if (((uint32_t)s - b) % 32 != 0) return;
-    int slot = atomicAdd(ngroups, 1);
-    int cnt = (int)min((uint32_t)32, e - (uint32_t)s);
-    groups[slot] = make_int4((int)s, cnt, (int)g.leaf[s], 0);
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool start = false;
+    int cnt = 0, L = 0;
+    if (s < n) {
+        L = g.leaf[s];
+        const u64 p = g.code[s] >> (3 * L);
+        if (s == 0 || (g.code[s - 1] >> (3 * L)) != p) {
+            start = true;
+        } else if (s >= 32 && (g.code[s - 32] >> (3 * L)) == p) {
+            uint32_t b, e;
+            start = leaf_range(g, s, b, e) && ((uint32_t)s - b) % 32 == 0;
+        }
+        if (start) {
+            cnt = 1;
+            while (cnt < 32 && s + cnt < n && (g.code[s + cnt] >> (3 * L)) == p) cnt++;
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, start);
+    if (!m) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ngroups, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (start) groups[base + __popc(m & ((1u << lane) - 1u))] = make_int4((int)s, cnt, L, 0);
 }
 
 cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* ngroups,

@@ -76,6 +76,7 @@ struct RoundDev {
     unsigned pre[8];
     int len[2];
     int ncand, nslow, nsrc, npairs, overflow, ncs;
+    int ndep;  // k = 1: candidates with a shell member of larger input index
     int changed[PD_FIX_ITERS];
     int fix_unconverged;
     int density_k1;
@@ -166,10 +167,12 @@ double host_next_band(double band, double band_max, int band_mode, unsigned long
 cudaError_t round_launch_finish(RoundDev* rd, cudaStream_t st);
 cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t n,
                                 SelBuffers& b, RoundDev* rd, cudaStream_t st);
+// dep: list of the candidates that have a shell member of larger input index
+// (the only ones condition (B) can reject; the fixpoint sweeps walk it).
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
                             const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
                             RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
-                            cudaStream_t st);
+                            int* dep, cudaStream_t st);
 cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
                                    int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
                                    cudaStream_t st);

@@ -18,6 +18,18 @@ namespace pd {
 #define FULLM 0xffffffffu
 #define PERSIST_BLOCKS (device_sms() * 8)
 
+// Appends s to list[*count ...] for every lane with want set, one atomic per
+// warp; every lane of the warp must call it.
+__device__ __forceinline__ void warp_append(bool want, int s, int* count, int* list) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(FULLM, want);
+    if (!m) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(FULLM, base, 0);
+    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = s;
+}
+
 // ------------------------------------------------------------------ setup
 __global__ void round_setup_kernel(RoundDev* rd) {
     if (threadIdx.x != 0) return;
@@ -34,6 +46,7 @@ __global__ void round_setup_kernel(RoundDev* rd) {
     rd->done = 0;
     rd->len[0] = rd->len[1] = 0;
     rd->ncand = rd->nslow = rd->nsrc = rd->npairs = rd->overflow = 0;
+    rd->ndep = 0;
     rd->removed = 0;
     rd->cap_over = 0;
     rd->fix_unconverged = 0;
@@ -188,23 +201,35 @@ __global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __
     int* oi = (pass & 1) ? bi1 : bi0;
     int64_t len = pass ? (int64_t)rd->len[(pass - 1) & 1] : n;
     uint32_t want = rd->pre[pass];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        u64 p;
-        int id;
-        if (pass) {
-            p = lp[i];
-            id = li[i];
-            if (sel_digit(p, id, pass) != want) continue;
-        } else {
-            if (!alive[i]) continue;
-            p = prim[i];
-            if ((uint32_t)(p >> 52) != want) continue;
-            id = pos[i].w;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count: the appends are aggregated per warp
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < len;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + lane;
+        u64 p = 0;
+        int id = 0;
+        bool take = false;
+        if (i < len) {
+            if (pass) {
+                p = lp[i];
+                id = li[i];
+                take = sel_digit(p, id, pass) == want;
+            } else if (alive[i]) {
+                p = prim[i];
+                take = (uint32_t)(p >> 52) == want;
+                if (take) id = pos[i].w;
+            }
         }
-        int slot = atomicAdd(&rd->len[pass & 1], 1);
-        op[slot] = p;
-        oi[slot] = id;
+        const unsigned m = __ballot_sync(FULLM, take);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&rd->len[pass & 1], __popc(m));
+        base = __shfl_sync(FULLM, base, 0);
+        if (take) {
+            const int slot = base + __popc(m & ((1u << lane) - 1u));
+            op[slot] = p;
+            oi[slot] = id;
+        }
     }
 }
 
@@ -212,31 +237,53 @@ __global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __
 __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
                                 const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
                                 const uint8_t* __restrict__ flg, int64_t n, int S, RoundDev* rd,
-                                uint8_t* inP, int* cand, int* slow) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n || !alive[s]) return;
-    u64 ps = prim[s];
-    const u64 tp = rd->tau_prim;
-    if (ps < tp) return;  // below the threshold on the primary: no index needed
-    int is = pos[s].w;
-    if (key_gt(tp, rd->tau_idx, ps, is)) return;
-    uint8_t fl = flg[s];
-    if (fl & 2) {
-        slow[atomicAdd(&rd->nslow, 1)] = (int)s;
-        return;
+                                uint8_t* inP, int* cand, int* slow, int* dep) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool c = false, sl = false, dp = false;
+    if (s < n && alive[s]) {
+        const u64 ps = prim[s];
+        const u64 tp = rd->tau_prim;
+        if (ps >= tp) {  // below the threshold on the primary: no index needed
+            const int is = pos[s].w;
+            if (!key_gt(tp, rd->tau_idx, ps, is)) {
+                const uint8_t fl = flg[s];
+                if (fl & 2) {
+                    sl = true;
+                } else {
+                    // the shell (points at the nearest distance) is the first
+                    // fl >> 2 stored neighbours; none: a lone point
+                    const int shell = fl >> 2;
+                    bool ok = shell == 0, larger = false;
+                    for (int i = 0; i < shell; i++) {
+                        const int x = nbr[s * S + i];
+                        const int ix = pos[x].w;
+                        if (key_gt(ps, is, prim[x], ix)) ok = true;
+                        if (ix > is) larger = true;
+                    }
+                    c = ok;
+                    dp = ok && larger;
+                }
+            }
+        }
     }
-    // the shell (points at the nearest distance) is the first fl >> 2 stored
-    // neighbours; none: a lone point
-    int shell = fl >> 2;
-    bool ok = shell == 0;
-    for (int i = 0; i < shell && !ok; i++) {
-        int x = nbr[s * S + i];
-        if (key_gt(ps, is, prim[x], pos[x].w)) ok = true;
+    // list appends aggregated per warp (every lane of the 256-thread blocks
+    // reaches them)
+    const unsigned mc = __ballot_sync(FULLM, c), ms = __ballot_sync(FULLM, sl);
+    int bc = 0, bs = 0;
+    if (lane == 0) {
+        if (mc) bc = atomicAdd(&rd->ncand, __popc(mc));
+        if (ms) bs = atomicAdd(&rd->nslow, __popc(ms));
     }
-    if (ok) {
+    bc = __shfl_sync(FULLM, bc, 0);
+    bs = __shfl_sync(FULLM, bs, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (c) {
         inP[s] = 1;
-        cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+        cand[bc + __popc(mc & lt)] = (int)s;
     }
+    if (sl) slow[bs + __popc(ms & lt)] = (int)s;
+    warp_append(dp, (int)s, &rd->ndep, dep);
 }
 
 // overflowing shells: accept iff every live point at distance d1 has a
@@ -300,7 +347,7 @@ __global__ void k1d_fix_kernel(const int* __restrict__ cand, const int4* __restr
                                const uint8_t* __restrict__ inP, uint8_t* rej, int iter,
                                RoundDev* rd) {
     if (iter > 0 && !rd->changed[iter - 1]) return;
-    int nc = rd->ncand;
+    int nc = rd->ndep;  // cand: the dep list (only its members can be rejected)
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
         int s = cand[t];
         if (rej[s]) continue;
@@ -321,11 +368,9 @@ __global__ void kkd_accept_kernel(const uint8_t* __restrict__ fq_flag, const u64
                                   const u64* __restrict__ fprim, int64_t n, RoundDev* rd,
                                   uint8_t* inP, int* cand) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n || !fq_flag[s]) return;
-    if (fprim[s] == prim[s]) {
-        inP[s] = 1;
-        cand[atomicAdd(&rd->ncand, 1)] = (int)s;
-    }
+    bool acc = s < n && fq_flag[s] && fprim[s] == prim[s];
+    if (acc) inP[s] = 1;
+    warp_append(acc, (int)s, &rd->ncand, cand);
 }
 
 __global__ void pairs_fix_kernel(const int2* __restrict__ pairs, int pair_cap, const uint8_t* inP,
@@ -542,7 +587,7 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
                                  int k, RoundDev* rd, uint8_t* inP, int* cand, uint8_t* fq_flag,
                                  uint8_t* lq_flag, u64* lam, int* src) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool fq = false, lq = false;
+    bool fq = false, lq = false, isc = false, iss = false;
     if (s < n) {
         if (alive[s]) {
             u64 tp = rd->tau_prim;
@@ -585,7 +630,7 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
                 }
                 if (acc) {
                     inP[s] = 1;
-                    cand[atomicAdd(&rd->ncand, 1)] = (int)s;
+                    isc = true;
                 }
                 if (key_gt(ps, is, tp, ti) && band_nbr) {
                     // danger source: lam from the stored entries of key below tau
@@ -601,13 +646,15 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
                     }
                     if (cnt >= k) lam[s] = l;
                     else lq = true;
-                    src[atomicAdd(&rd->nsrc, 1)] = (int)s;
+                    iss = true;
                 }
             }
         }
         fq_flag[s] = fq ? 1 : 0;
         lq_flag[s] = lq ? 1 : 0;
     }
+    warp_append(isc, (int)s, &rd->ncand, cand);
+    warp_append(iss, (int)s, &rd->nsrc, src);
     unsigned c1 = __popc(__ballot_sync(FULLM, fq)), c2 = __popc(__ballot_sync(FULLM, lq));
     if ((threadIdx.x & 31) == 0) {
         if (c1) atomicAdd(&rd->tot_filtered, (unsigned long long)c1);
@@ -647,11 +694,12 @@ cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t*
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
                             const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
                             RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
-                            cudaStream_t st) {
-    k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, flg, n, S, rd, inP, cand, slow); note_launch();
+                            int* dep, cudaStream_t st) {
+    k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, flg, n, S, rd, inP, cand, slow,
+                                         dep); note_launch();
     k1d_slow_kernel<<<PERSIST_BLOCKS, 128, 0, st>>>(g, prim, alive, rk2, slow, rd, inP, cand); note_launch();
     for (int it = 0; it < PD_FIX_ITERS; it++) {
-        k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(cand, g.pos, nbr, flg, S, inP, rej, it, rd); note_launch();
+        k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(dep, g.pos, nbr, flg, S, inP, rej, it, rd); note_launch();
     }
     return cudaGetLastError();
 }

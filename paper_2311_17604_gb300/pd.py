@@ -24,7 +24,8 @@ PD_STATIC_MAX_POINTS = 65536
 EXPORTED = ["pd_ctx_create", "pd_ctx_destroy", "pd_strerror", "pd_last_error", "pd_build_grid",
             "pd_grid_free", "pd_knn_cost", "pd_decimate_count", "pd_decimate_ratio",
             "pd_grid_stats", "pd_decimate_host", "pd_knn_cost_static", "pd_decimate_batch",
-            "pd_autotune", "pd_decimate_wup",
+            "pd_autotune", "pd_decimate_wup", "pd_ctx_set_device_budget", "pd_ctx_memory",
+            "pd_ctx_reset_peaks",
             # pd_normals.h
             "pd_normals_pca", "pd_mlp_init", "pd_mlp_forward", "pd_mlp_grad", "pd_mlp_train",
             "pd_normals_mlp",
@@ -61,6 +62,13 @@ class pd_cost_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("term", ctypes.c_int32), ("weight", ctypes.c_double),
                 ("normals_dev", ctypes.c_void_p), ("band", ctypes.c_double),
                 ("reserved", ctypes.c_int32 * 6)]
+
+
+class pd_memory(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("device_peak", ctypes.c_uint64), ("host_bytes", ctypes.c_uint64),
+                ("host_peak", ctypes.c_uint64), ("tracked", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class pd_stats(ctypes.Structure):
@@ -248,6 +256,22 @@ class Context:
 
     def error(self) -> str:
         return lib().pd_last_error(self.h).decode()
+
+    def set_device_budget(self, nbytes: int, spill_min: int = 0):
+        """pd_ctx_set_device_budget: blocks beyond nbytes of device memory
+        (and cold blocks) go to pinned host memory that the kernels address
+        in place; 0 lifts the budget."""
+        self.check(lib().pd_ctx_set_device_budget(self.h, ctypes.c_uint64(int(nbytes)),
+                                                  ctypes.c_uint64(int(spill_min))),
+                   "pd_ctx_set_device_budget")
+
+    def memory(self) -> dict:
+        m = pd_memory()
+        self.check(lib().pd_ctx_memory(self.h, ctypes.byref(m)), "pd_ctx_memory")
+        return {f: getattr(m, f) for f, _ in m._fields_ if f != "reserved"}
+
+    def reset_peaks(self):
+        self.check(lib().pd_ctx_reset_peaks(self.h), "pd_ctx_reset_peaks")
 
     def check(self, rc, what):
         if rc:
