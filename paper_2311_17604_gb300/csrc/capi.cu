@@ -202,6 +202,7 @@ struct pd_grid {
     int S, k, density_k1;
     u64* prim;
     int* nbr;
+    int* nbr0;  // k = 1 density: nbr[s * S], stored apart so that it reads coalesced
     u64* rk2;
     uint8_t* flg;
     u64* hz;  // k+b buffer horizon
@@ -453,7 +454,7 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
                     g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64, g->glist,
-                    g->gcount, g->cmin};
+                    g->gcount, g->cmin, g->nbr0};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -601,6 +602,7 @@ int prepare_state(pd_grid* g, const pd_cost_params* cp) {
     g->density_k1 = dk1;
     if (!g->prim) ALLOC(g->prim, u64, g->n);
     if (!g->nbr) ALLOC(g->nbr, int, (size_t)g->n * S);
+    if (dk1 && !g->nbr0) ALLOC(g->nbr0, int, g->n);
     if (!g->rk2) ALLOC_COLD(g->rk2, u64, g->n);
     if (!g->flg) ALLOC(g->flg, uint8_t, g->n);
     if (!g->hz) ALLOC_COLD(g->hz, u64, g->n);
@@ -627,6 +629,7 @@ KnnArgs base_args(pd_grid* g, const pd_cost_params* cp) {
     a.rgb = g->rgb;
     a.nrm = g->nrm;
     a.nbr = g->nbr;
+    a.nbr0_out = g->density_k1 ? g->nbr0 : nullptr;
     a.prim_out = g->prim;
     a.rk2_out = g->rk2;
     a.flg_out = g->flg;
@@ -757,6 +760,13 @@ int compact_rebuild(pd_grid* g, bool remap_state) {
         CK(launch_remap(list, nl, g->nbr, nb2, newpos, g->ng, g->S, g->st));
         gfree(g, g->nbr);
         g->nbr = nb2;
+        if (g->nbr0) {
+            int* n02;
+            ALLOC(n02, int, cn);
+            CK(launch_remap(list, nl, g->nbr0, n02, newpos, g->ng, 1, g->st));
+            gfree(g, g->nbr0);
+            g->nbr0 = n02;
+        }
     }
     tmp.done(newpos);
     tmp.done(list);
@@ -857,6 +867,7 @@ BufView bufview(pd_grid* g, const pd_cost_params* cp) {
     b.pos = g->pos;
     b.prim = g->prim;
     b.nbr = g->nbr;
+    b.nbr0 = g->density_k1 ? g->nbr0 : nullptr;
     b.rk2 = g->rk2;
     b.flg = g->flg;
     b.hz = g->hz;
@@ -1072,20 +1083,23 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     }
     // ---- first neighbour pass
     {
-        unsigned long long* dpairs = g->d_u64 + 1;
-        CK(cudaMemsetAsync(dpairs, 0, sizeof(*dpairs), g->st));
-        Span t(T, &g->stats.ms_knn_first);
-        KnnArgs a = base_args(g, cp);
-        a.pairs_out = dpairs;
-        CK(launch_knn(view_of(g), a, g->st));
-    }
-    g->stats.q_first = g->ng;
-    {
-        unsigned long long pairs = 0;
-        CK(cudaMemcpyAsync(&pairs, g->d_u64 + 1, sizeof(pairs), cudaMemcpyDeviceToHost, g->st));
+        unsigned long long* dpairs;
+        RALLOC(dpairs, unsigned long long, PD_PAIR_SLOTS);
+        CK(cudaMemsetAsync(dpairs, 0, PD_PAIR_SLOTS * sizeof(*dpairs), g->st));
+        {
+            Span t(T, &g->stats.ms_knn_first);
+            KnnArgs a = base_args(g, cp);
+            a.pairs_out = dpairs;
+            CK(launch_knn(view_of(g), a, g->st));
+        }
+        unsigned long long hp[PD_PAIR_SLOTS];
+        CK(cudaMemcpyAsync(hp, dpairs, sizeof(hp), cudaMemcpyDeviceToHost, g->st));
         CK(cudaStreamSynchronize(g->st));
+        unsigned long long pairs = 0;
+        for (int i = 0; i < PD_PAIR_SLOTS; i++) pairs += hp[i];
         g->stats.pairs_first = (int64_t)pairs;
     }
+    g->stats.q_first = g->ng;
     int S = g->S;
     int Sf = filt_width(k);
     int kchk = g->density_k1 ? S : k;
@@ -1172,8 +1186,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
                 CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
             }
             if (g->density_k1) {
-                CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->flg, g->rk2, g->ng, S, rd, inP,
-                                   rej, cand, slow, dep, g->st));
+                CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->nbr0, g->flg, g->rk2, g->ng, S,
+                                   rd, inP, rej, cand, slow, dep, g->st));
             } else {
                 BufView bv = bufview(g, cp);
                 CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,

@@ -142,27 +142,54 @@ __global__ void radix_hist_kernel(const u64* __restrict__ keys, int64_t n, int s
     counts[(int64_t)t * nblk + blockIdx.x] = h[t];
 }
 
+// Scatter of one 8-bit digit.  The tile's keys are first placed in digit
+// order in shared memory (stable: sub-tile by sub-tile, warp by warp, lane by
+// lane), then written out in that order, so that consecutive threads write
+// consecutive addresses of one digit's run.  offs is the exclusive scan of the
+// digit-major [digit][tile] counts: the tile's own count of digit d is the gap
+// to the next entry (n at the very end).
 __global__ void radix_scatter_kernel(const u64* __restrict__ kin, const uint32_t* __restrict__ vin,
                                      u64* __restrict__ kout, uint32_t* __restrict__ vout,
                                      int64_t n, int shift, const uint32_t* __restrict__ offs,
                                      int nblk) {
+    __shared__ u64 sk[RS_TILE];
+    __shared__ uint32_t sv[RS_TILE];
     __shared__ uint32_t goff[256];
+    __shared__ uint32_t tpre[256];  // first slot of digit d in the tile's sorted order
     __shared__ uint32_t run[256];
+    __shared__ uint32_t wsum[8];
     __shared__ uint16_t wcnt[8][257];
-    int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    goff[t] = offs[(int64_t)t * nblk + blockIdx.x];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int64_t gi = (int64_t)t * nblk + blockIdx.x;
+    const uint32_t go = offs[gi];
+    const uint32_t next = gi + 1 < (int64_t)256 * nblk ? offs[gi + 1] : (uint32_t)n;
+    goff[t] = go;
     run[t] = 0;
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    for (int j = 0; j < 8; j++) {
+    // exclusive scan of the tile's per-digit counts over the 256 digits
+    {
+        const uint32_t c = next - go;
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ww++) before += wsum[ww];
+        tpre[t] = before + x - c;
+    }
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int j = 0; j < RS_TILE / 256; j++) {
         for (int x = t; x < 8 * 257; x += 256) (&wcnt[0][0])[x] = 0;
         __syncthreads();
-        int64_t i = base + j * 256 + t;
-        bool valid = i < n;
-        u64 k = valid ? kin[i] : 0ull;
-        uint32_t v = valid ? vin[i] : 0u;
-        int d = valid ? (int)((k >> shift) & 255) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int lrank = __popc(peers & ((1u << lane) - 1u));
+        const int64_t i = base + j * 256 + t;
+        const bool valid = i < n;
+        const u64 k = valid ? kin[i] : 0ull;
+        const uint32_t v = valid ? vin[i] : 0u;
+        const int d = valid ? (int)((k >> shift) & 255) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int lrank = __popc(peers & ((1u << lane) - 1u));
         if (lane == __ffs(peers) - 1) wcnt[w][d] = (uint16_t)__popc(peers);
         __syncthreads();
         {
@@ -176,11 +203,19 @@ __global__ void radix_scatter_kernel(const u64* __restrict__ kin, const uint32_t
         }
         __syncthreads();
         if (valid) {
-            uint32_t p = goff[d] + wcnt[w][d] + (uint32_t)lrank;
-            kout[p] = k;
-            vout[p] = v;
+            const uint32_t lp = tpre[d] + wcnt[w][d] + (uint32_t)lrank;
+            sk[lp] = k;
+            sv[lp] = v;
         }
-        __syncthreads();
+        __syncthreads();  // wcnt is cleared at the top of the next sub-tile
+    }
+    const int tn = (int)min((int64_t)RS_TILE, n - base);
+    for (int x = t; x < tn; x += 256) {
+        const u64 k = sk[x];
+        const int d = (int)((k >> shift) & 255);
+        const uint32_t p = goff[d] + ((uint32_t)x - tpre[d]);
+        kout[p] = k;
+        vout[p] = sv[x];
     }
 }
 
@@ -319,8 +354,7 @@ __global__ void node_count_kernel(const u64* __restrict__ code, const uint8_t* _
         int lo = leaf[i];
         c = hi >= lo ? (unsigned)(hi - lo + 1) : 0u;
     }
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+    block_add(count, c);
 }
 
 cudaError_t launch_node_count(const u64* code, const uint8_t* leaf, int64_t n, int B,
@@ -379,7 +413,6 @@ __device__ inline bool leaf_range(const GridView& g, int64_t s, uint32_t& b, uin
 // 32, b the leaf's first position (from the cell table).
 __global__ void leaf_groups_kernel(GridView g, int64_t n, int4* groups, int* ngroups) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     bool start = false;
     int cnt = 0, L = 0;
     if (s < n) {
@@ -396,12 +429,8 @@ __global__ void leaf_groups_kernel(GridView g, int64_t n, int4* groups, int* ngr
             while (cnt < 32 && s + cnt < n && (g.code[s + cnt] >> (3 * L)) == p) cnt++;
         }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, start);
-    if (!m) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(ngroups, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (start) groups[base + __popc(m & ((1u << lane) - 1u))] = make_int4((int)s, cnt, L, 0);
+    const int slot = block_append(start, ngroups);
+    if (start) groups[slot] = make_int4((int)s, cnt, L, 0);
 }
 
 cudaError_t launch_leaf_groups(const GridView& g, int64_t n, int4* groups, int* ngroups,

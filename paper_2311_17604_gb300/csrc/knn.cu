@@ -383,6 +383,7 @@ __device__ __forceinline__ void write_result(const KnnArgs& a, int q, const TL& 
                 shell += (h && top.dist(i) == d0) ? 1 : 0;
                 a.nbr[(int64_t)q * S + i] = h ? top.ident(i) : -1;
             }
+            if (!W && a.nbr0_out) a.nbr0_out[q] = top.has(0) ? top.ident(0) : -1;
             a.prim_out[q] = key_prim_d2(d0);
             a.rk2_out[q] = d0;
             a.flg_out[q] = (uint8_t)((shell >= 2 ? 1 : 0) | (shell == S ? 2 : 0) | (shell << 2));
@@ -574,7 +575,13 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
                                                         bz, cx, cy, cz, sp, sk, so, wpairs);
         L++;
     }
-    if (a.pairs_out && lane == 0 && wpairs) atomicAdd(a.pairs_out, wpairs);
+    // spread over PD_PAIR_SLOTS counters by SM (one address would serialise
+    // in L2; the SM id is read here, so it holds no register during the search)
+    if (a.pairs_out && lane == 0 && wpairs) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        atomicAdd(&a.pairs_out[smid % PD_PAIR_SLOTS], wpairs);
+    }
 }
 
 template <int S, int FILT, bool W, bool LIST>
@@ -788,13 +795,8 @@ __global__ void flagged_groups_kernel(const int4* __restrict__ groups, int ngrou
         int4 G = groups[gid];
         for (int i = 0; i < G.y && !any; i++) any = qflag[G.x + i] != 0;
     }
-    unsigned bal = __ballot_sync(FULLM, any);
-    if (!bal) return;
-    int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(gcount, __popc(bal));
-    base = __shfl_sync(FULLM, base, 0);
-    if (any) glist[base + __popc(bal & ((1u << lane) - 1u))] = gid;
+    const int slot = block_append(any, gcount);
+    if (any) glist[slot] = gid;
 }
 
 template <int S, int FILT>

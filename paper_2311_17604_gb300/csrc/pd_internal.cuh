@@ -172,6 +172,70 @@ __device__ inline unsigned long long sqd(int4 a, int4 b) {
 extern long long g_launch_count;
 inline void note_launch() { __atomic_fetch_add(&g_launch_count, 1, __ATOMIC_RELAXED); }
 
+// Block-level aggregation of counters and list appends: one global atomic
+// per block instead of one per warp (atomics on one address serialise in L2,
+// and a full-grid kernel over a billion points has 31M warps).  Every thread
+// of the block must make the call (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ void block_add(unsigned long long* dst, unsigned long long v) {
+    __shared__ unsigned long long s_part[32];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // s_part may still be read by a previous call
+    if (lane == 0) s_part[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += s_part[i];
+        if (t) atomicAdd(dst, t);
+    }
+}
+// Two counters at once (one reduction, two atomics per block).
+__device__ __forceinline__ void block_add2(unsigned long long* d1, unsigned long long v1,
+                                           unsigned long long* d2, unsigned long long v2) {
+    __shared__ unsigned long long s_p1[32], s_p2[32];
+    for (int o = 16; o; o >>= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        s_p1[w] = v1;
+        s_p2[w] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t1 = 0, t2 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            t1 += s_p1[i];
+            t2 += s_p2[i];
+        }
+        if (t1) atomicAdd(d1, t1);
+        if (t2) atomicAdd(d2, t2);
+    }
+}
+// Appends for every thread with want set; returns the thread's slot in the
+// list (meaningful where want is set).
+__device__ __forceinline__ int block_append(bool want, int* count) {
+    __shared__ int s_w[33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    __syncthreads();  // s_w may still be read by a previous call
+    if (lane == 0) s_w[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            int c = s_w[i];
+            s_w[i] = acc;
+            acc += c;
+        }
+        s_w[32] = acc ? atomicAdd(count, acc) : 0;
+    }
+    __syncthreads();
+    return s_w[32] + s_w[w] + __popc(m & ((1u << lane) - 1u));
+}
+
 // Streaming multiprocessors of the current device (queried once per device
 // and cached); persistent and grid-stride launches size their grids from it.
 int device_sms();

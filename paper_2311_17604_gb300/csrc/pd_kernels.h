@@ -91,6 +91,7 @@ struct SelBuffers {
 
 // ---------------------------------------------------------------- knn.cu
 enum { FILT_NONE = 0, FILT_BELOW_SELF = 1, FILT_BELOW_TAU = 2 };
+#define PD_PAIR_SLOTS 64
 
 struct KnnArgs {
     const int4* groups;
@@ -112,6 +113,7 @@ struct KnnArgs {
     const float4* nrm;
     // outputs (full / re-query mode)
     int* nbr;                 // n x S Morton positions
+    int* nbr0_out;            // optional: the first stored entry again, one int per point
     u64* prim_out;            // key primary
     u64* rk2_out;             // k-th squared distance
     uint8_t* flg_out;
@@ -120,7 +122,8 @@ struct KnnArgs {
     // outputs (filter modes)
     u64* fprim_out;           // FILT_BELOW_SELF: key primary over lower keys
     u64* lam_out;             // FILT_BELOW_TAU: k-th squared distance over keys < tau
-    unsigned long long* pairs_out;  // optional: + (query, candidate) pairs scanned
+    unsigned long long* pairs_out;  // optional: + (query, candidate) pairs scanned, spread
+                                    //   over PD_PAIR_SLOTS counters (their sum is the count)
     const u64* cmin;          // filtered searches: least live key primary of every aligned
                               //   32-position chunk (chunks above the threshold are skipped)
     const int* glist;         // group-list mode: process groups glist[0 .. *gcount)
@@ -169,10 +172,11 @@ cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t*
                                 SelBuffers& b, RoundDev* rd, cudaStream_t st);
 // dep: list of the candidates that have a shell member of larger input index
 // (the only ones condition (B) can reject; the fixpoint sweeps walk it).
+// nbr0: the first stored entries apart (may be NULL).
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
-                            const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
-                            RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
-                            int* dep, cudaStream_t st);
+                            const int* nbr, const int* nbr0, const uint8_t* flg, const u64* rk2,
+                            int64_t n, int S, RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand,
+                            int* slow, int* dep, cudaStream_t st);
 cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
                                    int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
                                    cudaStream_t st);
@@ -190,6 +194,7 @@ struct BufView {  // the k+b neighbour buffer of every point
     const int4* pos;
     u64* prim;
     int* nbr;
+    int* nbr0;  // optional (k = 1 density): nbr[s * S] kept apart, read coalesced
     u64* rk2;
     uint8_t* flg;
     u64* hz;

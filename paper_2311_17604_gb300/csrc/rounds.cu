@@ -46,8 +46,7 @@ __global__ void dup_flag_kernel(const u64* __restrict__ code, const int4* __rest
         dup[s] = f;
         c = f;
     }
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULLM, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+    block_add(count, c);
 }
 
 // remove flagged duplicates whose input index is >= idx_min
@@ -480,8 +479,7 @@ __global__ void remove_kernel(const int* __restrict__ cand, const int* __restric
         inP[s] = 0;
         rej[s] = 0;
     }
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULLM, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(removed, (unsigned long long)c);
+    block_add(removed, c);
 }
 
 __global__ void keep_kernel(const int4* __restrict__ pos, const uint8_t* __restrict__ alive,

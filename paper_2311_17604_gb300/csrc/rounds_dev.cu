@@ -18,16 +18,11 @@ namespace pd {
 #define FULLM 0xffffffffu
 #define PERSIST_BLOCKS (device_sms() * 8)
 
-// Appends s to list[*count ...] for every lane with want set, one atomic per
-// warp; every lane of the warp must call it.
-__device__ __forceinline__ void warp_append(bool want, int s, int* count, int* list) {
-    const int lane = threadIdx.x & 31;
-    const unsigned m = __ballot_sync(FULLM, want);
-    if (!m) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(FULLM, base, 0);
-    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = s;
+// Appends s to list[*count ...] for every thread with want set, one atomic
+// per block; every thread of the block must call it.
+__device__ __forceinline__ void list_append(bool want, int s, int* count, int* list) {
+    const int slot = block_append(want, count);
+    if (want) list[slot] = s;
 }
 
 // ------------------------------------------------------------------ setup
@@ -201,11 +196,10 @@ __global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __
     int* oi = (pass & 1) ? bi1 : bi0;
     int64_t len = pass ? (int64_t)rd->len[(pass - 1) & 1] : n;
     uint32_t want = rd->pre[pass];
-    const int lane = threadIdx.x & 31;
-    // warp-uniform trip count: the appends are aggregated per warp
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < len;
+    // block-uniform trip count: the appends are aggregated per block
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < len;
          i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + lane;
+        const int64_t i = i0 + threadIdx.x;
         u64 p = 0;
         int id = 0;
         bool take = false;
@@ -220,13 +214,8 @@ __global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __
                 if (take) id = pos[i].w;
             }
         }
-        const unsigned m = __ballot_sync(FULLM, take);
-        if (!m) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&rd->len[pass & 1], __popc(m));
-        base = __shfl_sync(FULLM, base, 0);
+        const int slot = block_append(take, &rd->len[pass & 1]);
         if (take) {
-            const int slot = base + __popc(m & ((1u << lane) - 1u));
             op[slot] = p;
             oi[slot] = id;
         }
@@ -236,10 +225,10 @@ __global__ void seld_compact_kernel(const u64* __restrict__ prim, const int4* __
 // ------------------------------------------------------------------ k = 1
 __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
                                 const uint8_t* __restrict__ alive, const int* __restrict__ nbr,
+                                const int* __restrict__ nbr0,
                                 const uint8_t* __restrict__ flg, int64_t n, int S, RoundDev* rd,
                                 uint8_t* inP, int* cand, int* slow, int* dep) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     bool c = false, sl = false, dp = false;
     if (s < n && alive[s]) {
         const u64 ps = prim[s];
@@ -256,7 +245,7 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
                     const int shell = fl >> 2;
                     bool ok = shell == 0, larger = false;
                     for (int i = 0; i < shell; i++) {
-                        const int x = nbr[s * S + i];
+                        const int x = i == 0 && nbr0 ? nbr0[s] : nbr[s * S + i];
                         const int ix = pos[x].w;
                         if (key_gt(ps, is, prim[x], ix)) ok = true;
                         if (ix > is) larger = true;
@@ -267,23 +256,11 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
             }
         }
     }
-    // list appends aggregated per warp (every lane of the 256-thread blocks
-    // reaches them)
-    const unsigned mc = __ballot_sync(FULLM, c), ms = __ballot_sync(FULLM, sl);
-    int bc = 0, bs = 0;
-    if (lane == 0) {
-        if (mc) bc = atomicAdd(&rd->ncand, __popc(mc));
-        if (ms) bs = atomicAdd(&rd->nslow, __popc(ms));
-    }
-    bc = __shfl_sync(FULLM, bc, 0);
-    bs = __shfl_sync(FULLM, bs, 0);
-    const unsigned lt = (1u << lane) - 1u;
-    if (c) {
-        inP[s] = 1;
-        cand[bc + __popc(mc & lt)] = (int)s;
-    }
-    if (sl) slow[bs + __popc(ms & lt)] = (int)s;
-    warp_append(dp, (int)s, &rd->ndep, dep);
+    // list appends aggregated per block (every thread reaches them)
+    if (c) inP[s] = 1;
+    list_append(c, (int)s, &rd->ncand, cand);
+    list_append(sl, (int)s, &rd->nslow, slow);
+    list_append(dp, (int)s, &rd->ndep, dep);
 }
 
 // overflowing shells: accept iff every live point at distance d1 has a
@@ -370,7 +347,7 @@ __global__ void kkd_accept_kernel(const uint8_t* __restrict__ fq_flag, const u64
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool acc = s < n && fq_flag[s] && fprim[s] == prim[s];
     if (acc) inP[s] = 1;
-    warp_append(acc, (int)s, &rd->ncand, cand);
+    list_append(acc, (int)s, &rd->ncand, cand);
 }
 
 __global__ void pairs_fix_kernel(const int2* __restrict__ pairs, int pair_cap, const uint8_t* inP,
@@ -428,8 +405,7 @@ __global__ void dirtyd_kernel(const uint8_t* __restrict__ alive, const int* __re
         }
         dirty[s] = d ? 1 : 0;
     }
-    unsigned c = __popc(__ballot_sync(FULLM, d));
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->tot_requery, (unsigned long long)c);
+    block_add(&rd->tot_requery, d ? 1ull : 0ull);
 }
 
 // ------------------------------------------------------------------ k = 1 buffer
@@ -453,7 +429,11 @@ __global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
         bool shell_hit = false;
         if (alive[s]) {
             int shell = b.flg[s] >> 2;
-            for (int i = 0; i < shell && !shell_hit; i++) shell_hit = !alive[b.nbr[s * S + i]];
+            if (shell > 0) {
+                // the first entry from its coalesced copy (most shells hold one point)
+                shell_hit = !alive[b.nbr0 ? b.nbr0[s] : b.nbr[s * S]];
+                for (int i = 1; i < shell && !shell_hit; i++) shell_hit = !alive[b.nbr[s * S + i]];
+            }
         }
         if (shell_hit) {
             int ids[K1_SMAX];
@@ -489,6 +469,7 @@ __global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
 #pragma unroll
                     for (int i = 0; i < K1_SMAX; i++)
                         if (i < S) b.nbr[s * S + i] = ids[i];
+                    if (b.nbr0) b.nbr0[s] = ids[0];
                     upd = true;
                 } else {
                     dv = 1;
@@ -498,11 +479,7 @@ __global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
         }
         dirty[s] = dv;
     }
-    unsigned cu = __popc(__ballot_sync(FULLM, upd)), cr = __popc(__ballot_sync(FULLM, req));
-    if ((threadIdx.x & 31) == 0) {
-        if (cu) atomicAdd(&rd->tot_updated, (unsigned long long)cu);
-        if (cr) atomicAdd(&rd->tot_requery, (unsigned long long)cr);
-    }
+    block_add2(&rd->tot_updated, upd ? 1ull : 0ull, &rd->tot_requery, req ? 1ull : 0ull);
 }
 
 // ------------------------------------------------------------------ k+b buffer
@@ -570,11 +547,7 @@ __global__ void kkd_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
         }
         dirty[s] = dv;
     }
-    unsigned cu = __popc(__ballot_sync(FULLM, upd)), cr = __popc(__ballot_sync(FULLM, req));
-    if ((threadIdx.x & 31) == 0) {
-        if (cu) atomicAdd(&rd->tot_updated, (unsigned long long)cu);
-        if (cr) atomicAdd(&rd->tot_requery, (unsigned long long)cr);
-    }
+    block_add2(&rd->tot_updated, upd ? 1ull : 0ull, &rd->tot_requery, req ? 1ull : 0ull);
 }
 
 // Candidate test (k >= 2) using the stored buffer where it suffices:
@@ -653,13 +626,9 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
         fq_flag[s] = fq ? 1 : 0;
         lq_flag[s] = lq ? 1 : 0;
     }
-    warp_append(isc, (int)s, &rd->ncand, cand);
-    warp_append(iss, (int)s, &rd->nsrc, src);
-    unsigned c1 = __popc(__ballot_sync(FULLM, fq)), c2 = __popc(__ballot_sync(FULLM, lq));
-    if ((threadIdx.x & 31) == 0) {
-        if (c1) atomicAdd(&rd->tot_filtered, (unsigned long long)c1);
-        if (c2) atomicAdd(&rd->tot_lambda, (unsigned long long)c2);
-    }
+    list_append(isc, (int)s, &rd->ncand, cand);
+    list_append(iss, (int)s, &rd->nsrc, src);
+    block_add2(&rd->tot_filtered, fq ? 1ull : 0ull, &rd->tot_lambda, lq ? 1ull : 0ull);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -692,11 +661,11 @@ cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t*
 }
 
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
-                            const int* nbr, const uint8_t* flg, const u64* rk2, int64_t n, int S,
-                            RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand, int* slow,
-                            int* dep, cudaStream_t st) {
-    k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, flg, n, S, rd, inP, cand, slow,
-                                         dep); note_launch();
+                            const int* nbr, const int* nbr0, const uint8_t* flg, const u64* rk2,
+                            int64_t n, int S, RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand,
+                            int* slow, int* dep, cudaStream_t st) {
+    k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, nbr0, flg, n, S, rd, inP, cand,
+                                         slow, dep); note_launch();
     k1d_slow_kernel<<<PERSIST_BLOCKS, 128, 0, st>>>(g, prim, alive, rk2, slow, rd, inP, cand); note_launch();
     for (int it = 0; it < PD_FIX_ITERS; it++) {
         k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(dep, g.pos, nbr, flg, S, inP, rej, it, rd); note_launch();

@@ -135,8 +135,7 @@ __global__ void wup_pick_kernel(const BufView b, const uint8_t* __restrict__ ali
         }
         pick[s] = ok ? 1 : 0;
     }
-    unsigned c = __popc(__ballot_sync(FULLM, ok));
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&rd->removed, (unsigned long long)c);
+    block_add(&rd->removed, ok ? 1ull : 0ull);
 }
 
 __global__ void wup_remove_kernel(const uint8_t* __restrict__ pick, int64_t n, uint8_t* alive) {
@@ -189,8 +188,7 @@ __global__ void wup_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
             }
         }
     }
-    unsigned cu = __popc(__ballot_sync(FULLM, upd));
-    if ((threadIdx.x & 31) == 0 && cu) atomicAdd(&rd->tot_updated, (unsigned long long)cu);
+    block_add(&rd->tot_updated, upd ? 1ull : 0ull);
 }
 
 #define WGRID(n) (unsigned)(((n) + 255) / 256), 256
