@@ -217,6 +217,7 @@ struct pd_grid {
     double ms_grid;  // device time of the pd_build_grid call
     int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8;
                      //   the rest of the 8 stored are kept below the reported horizon)
+    int k1_exact_rq; // ... in the re-searches of the rounds
     int sparse_rq;   // k = 1 density re-searches over a list of the flagged points, 4 lanes
                      //   each (else a warp per flagged leaf group)
     double compact_at;  // the rounds compact the grid once live < compact_at * built
@@ -489,6 +490,7 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     // diagnostic: exact depth of the k = 1 searches (any depth gives the same
     // result; the stored list is complete below the reported horizon)
     g->k1_exact = getenv("PD_K1_EXACT") ? atoi(getenv("PD_K1_EXACT")) : 2;
+    g->k1_exact_rq = getenv("PD_K1_EXACT_RQ") ? atoi(getenv("PD_K1_EXACT_RQ")) : 3;
     // diagnostic: 0 runs the re-searches per leaf group (same results)
     g->sparse_rq = getenv("PD_SPARSE_REQUERY") ? atoi(getenv("PD_SPARSE_REQUERY")) : 1;
     g->compact_at = getenv("PD_COMPACT_AT") ? atof(getenv("PD_COMPACT_AT")) : 0.7;
@@ -893,6 +895,7 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
         // over their own cells (the weighted and k >= 2 rounds re-search few
         // points per round, where a warp per flagged group measured faster)
         ArenaUse au;
+        if (g->k1_exact_rq > 0) a.r_exact = g->k1_exact_rq;
         CK(stable_compact(qflag, g->ng, g->rq_list, g->rq_count, round_scratch(g, &au), g->st));
         CK(launch_knn_sparse(view_of(g), a, g->rq_list, g->rq_count, g->ng, g->st));
         return PD_OK;

@@ -230,8 +230,10 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
                                 uint8_t* inP, int* cand, int* slow, int* dep) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool c = false, sl = false, dp = false;
-    if (s < n && alive[s]) {
-        const u64 ps = prim[s];
+    const bool in = s < n;
+    const uint8_t al = in ? alive[s] : 0;
+    const u64 ps = in ? prim[s] : 0;  // loaded beside the alive flag, not after it
+    if (al) {
         const u64 tp = rd->tau_prim;
         if (ps >= tp) {  // below the threshold on the primary: no index needed
             const int is = pos[s].w;
@@ -426,14 +428,16 @@ __global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, 
         uint8_t dv = 0;
         // only a removed shell member changes the key or the shell; removed
         // entries past the shell stay stored (stale) until the shell changes
+        // the point's flag, shell size and first entry are loaded together
+        // (the first entry from its coalesced copy: most shells hold one
+        // point), so that only the entry's alive flag waits on them
         bool shell_hit = false;
-        if (alive[s]) {
-            int shell = b.flg[s] >> 2;
-            if (shell > 0) {
-                // the first entry from its coalesced copy (most shells hold one point)
-                shell_hit = !alive[b.nbr0 ? b.nbr0[s] : b.nbr[s * S]];
-                for (int i = 1; i < shell && !shell_hit; i++) shell_hit = !alive[b.nbr[s * S + i]];
-            }
+        const uint8_t al = alive[s];
+        const int shell = b.flg[s] >> 2;
+        const int x0 = b.nbr0 ? b.nbr0[s] : b.nbr[s * S];
+        if (al && shell > 0) {
+            shell_hit = !alive[x0];
+            for (int i = 1; i < shell && !shell_hit; i++) shell_hit = !alive[b.nbr[s * S + i]];
         }
         if (shell_hit) {
             int ids[K1_SMAX];
