@@ -1167,6 +1167,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     h.band_max = band_max;
     h.density_k1 = g->density_k1;
     h.band_mode = getenv("PD_BAND_MODE") ? atoi(getenv("PD_BAND_MODE")) : 1;
+    h.fix_iters = g->density_k1 ? PD_FIX_ITERS : PD_FIX_ITERS_KK;
+    if (g->density_k1 && getenv("PD_FIX_SWEEPS"))  // fewer sweeps: more rounds settled on the host
+        h.fix_iters = std::max(1, std::min(PD_FIX_ITERS, atoi(getenv("PD_FIX_SWEEPS"))));
     CK(cudaMemcpyAsync(rd, &h, sizeof(h), cudaMemcpyHostToDevice, g->st));
     int64_t built = live;
     // small clouds are bound by launches: from the third round on, a round's
@@ -1190,7 +1193,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             }
             if (g->density_k1) {
                 CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->nbr0, g->flg, g->rk2, g->ng, S,
-                                   rd, inP, rej, cand, slow, dep, g->st));
+                                   rd, inP, rej, cand, slow, dep, h.fix_iters, g->st));
             } else {
                 BufView bv = bufview(g, cp);
                 CK(round_launch_kk_cand2(bv, g->alive, g->ng, S, k, rd, inP, cand, fqf, dgf, lam, src,

@@ -62,7 +62,8 @@ cudaError_t launch_take_xyz(const int* list, const int* count, int64_t cap, cons
                             int32_t* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- round state
-#define PD_FIX_ITERS 8
+#define PD_FIX_ITERS 32    // device fixpoint sweeps of a k = 1 round (the most)
+#define PD_FIX_ITERS_KK 8  // ... of a k >= 2 round (danger pairs)
 
 // Per-round control block in device memory (read by the host once per round).
 struct RoundDev {
@@ -81,6 +82,7 @@ struct RoundDev {
     int fix_unconverged;
     int density_k1;
     int band_mode;  // 0: shrink on overflow only; 1: also on poor yield
+    int fix_iters;  // device fixpoint sweeps per round (<= PD_FIX_ITERS)
 };
 
 struct SelBuffers {
@@ -176,7 +178,7 @@ cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t*
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
                             const int* nbr, const int* nbr0, const uint8_t* flg, const u64* rk2,
                             int64_t n, int S, RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand,
-                            int* slow, int* dep, cudaStream_t st);
+                            int* slow, int* dep, int fix_iters, cudaStream_t st);
 cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, const u64* fprim,
                                    int64_t n, RoundDev* rd, uint8_t* inP, int* cand,
                                    cudaStream_t st);

@@ -374,8 +374,11 @@ __global__ void removed_kernel(const int* __restrict__ cand, uint8_t* inP, uint8
                                uint8_t* alive, RoundDev* rd) {
     __shared__ int hold;
     if (threadIdx.x == 0) {
-        hold = rd->overflow || rd->changed[PD_FIX_ITERS - 1];
-        if (hold && blockIdx.x == 0) rd->fix_unconverged = rd->changed[PD_FIX_ITERS - 1];
+        int fi = rd->fix_iters;
+        if (fi < 1 || fi > PD_FIX_ITERS) fi = PD_FIX_ITERS;
+        const int last = rd->changed[fi - 1];
+        hold = rd->overflow || last;
+        if (hold && blockIdx.x == 0) rd->fix_unconverged = last;
     }
     __syncthreads();
     if (hold) return;
@@ -667,11 +670,12 @@ cudaError_t round_launch_select(const u64* prim, const int4* pos, const uint8_t*
 cudaError_t round_launch_k1(const GridView& g, const u64* prim, const uint8_t* alive,
                             const int* nbr, const int* nbr0, const uint8_t* flg, const u64* rk2,
                             int64_t n, int S, RoundDev* rd, uint8_t* inP, uint8_t* rej, int* cand,
-                            int* slow, int* dep, cudaStream_t st) {
+                            int* slow, int* dep, int fix_iters, cudaStream_t st) {
+    if (fix_iters < 1 || fix_iters > PD_FIX_ITERS) return cudaErrorInvalidValue;
     k1d_cand_kernel<<<GRID1(n), 0, st>>>(prim, g.pos, alive, nbr, nbr0, flg, n, S, rd, inP, cand,
                                          slow, dep); note_launch();
     k1d_slow_kernel<<<PERSIST_BLOCKS, 128, 0, st>>>(g, prim, alive, rk2, slow, rd, inP, cand); note_launch();
-    for (int it = 0; it < PD_FIX_ITERS; it++) {
+    for (int it = 0; it < fix_iters; it++) {
         k1d_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(dep, g.pos, nbr, flg, S, inP, rej, it, rd); note_launch();
     }
     return cudaGetLastError();
@@ -686,7 +690,7 @@ cudaError_t round_launch_kk_accept(const uint8_t* fq_flag, const u64* prim, cons
 
 cudaError_t round_launch_pairs_fix(const int2* pairs, int pair_cap, const uint8_t* inP,
                                    uint8_t* rej, RoundDev* rd, cudaStream_t st) {
-    for (int it = 0; it < PD_FIX_ITERS; it++) {
+    for (int it = 0; it < PD_FIX_ITERS_KK; it++) {
         pairs_fix_kernel<<<PERSIST_BLOCKS, 256, 0, st>>>(pairs, pair_cap, inP, rej, it, rd); note_launch();
     }
     return cudaGetLastError();

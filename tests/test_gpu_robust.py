@@ -124,3 +124,18 @@ def test_long_tie_chains_settle_on_host(pd):
         g.free()
         assert np.array_equal(keep, oracle.decimate(x, 1, m))
     ctx.close()
+
+
+@pytest.mark.parametrize("sweeps", ["1", "3"])
+def test_k1_rounds_settled_on_host_after_few_sweeps(pd, monkeypatch, sweeps):
+    """PD_FIX_SWEEPS caps the device sweeps of the k = 1 fixpoint, so that
+    ordinary rounds are settled on the host; the result is the oracle's."""
+    s = synth.room_scan(seed=6, n_az=500, n_el=100)
+    m = oracle.target_count(s.n, 0.2)
+    monkeypatch.setenv("PD_FIX_SWEEPS", sweeps)
+    ctx = pd.Context()
+    g = pd.Grid(ctx, torch.from_numpy(s.xyz).cuda())
+    keep = pd.pd_decimate_count(g, m, k=1).cpu().numpy()
+    g.free()
+    ctx.close()
+    assert np.array_equal(keep, oracle.decimate(s.xyz, 1, m))
