@@ -221,6 +221,7 @@ struct pd_grid {
     int sparse_rq;   // k = 1 density re-searches over a list of the flagged points, 4 lanes
                      //   each (else a warp per flagged leaf group)
     double compact_at;  // the rounds compact the grid once live < compact_at * built
+                        //   (0: the cost's default)
     int* rq_list;    // during a decimation: flagged Morton positions and their count
     int* rq_count;
     char* arena;     // during a decimation: scratch of the per-round compactions
@@ -493,8 +494,9 @@ extern "C" int pd_build_grid(pd_ctx* ctx, const int32_t* xyz_dev, const uint8_t*
     g->k1_exact_rq = getenv("PD_K1_EXACT_RQ") ? atoi(getenv("PD_K1_EXACT_RQ")) : 3;
     // diagnostic: 0 runs the re-searches per leaf group (same results)
     g->sparse_rq = getenv("PD_SPARSE_REQUERY") ? atoi(getenv("PD_SPARSE_REQUERY")) : 1;
-    g->compact_at = getenv("PD_COMPACT_AT") ? atof(getenv("PD_COMPACT_AT")) : 0.7;
-    if (!(g->compact_at > 0.0 && g->compact_at < 1.0)) g->compact_at = 0.7;
+    // 0: by cost (decimate_impl); PD_COMPACT_AT overrides
+    g->compact_at = getenv("PD_COMPACT_AT") ? atof(getenv("PD_COMPACT_AT")) : 0.0;
+    if (!(g->compact_at > 0.0 && g->compact_at < 1.0)) g->compact_at = 0.0;
     g->n = n;
     g->ng = n;
     g->T = T;
@@ -1351,7 +1353,11 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         live = h.live;
         if (live <= m) break;
         // every live point now stores live neighbours only: safe to compact
-        if ((double)live < g->compact_at * (double)built) {
+        // k = 1 re-searches are cheap next to a rebuild (measured best at
+        // 0.6 on the billion-point scan); the k >= 2 rounds are many and
+        // scan their dead points every round (0.7)
+        const double at = g->compact_at > 0.0 ? g->compact_at : (g->density_k1 ? 0.6 : 0.7);
+        if ((double)live < at * (double)built) {
             Span t(T, &g->stats.ms_build);
             rc = compact_rebuild(g, true);
             if (rc) return rc;
