@@ -423,7 +423,10 @@ __global__ void dirtyd_kernel(const uint8_t* __restrict__ alive, const int* __re
 // when no stored entry is left, the point is searched again.
 #define K1_SMAX 8
 
-__global__ void k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
+// 40 registers, 6 blocks of 256 per SM: the update waits on dependent loads,
+// and more threads in flight measured faster (rules of the 100M-point scan
+// 52.9 -> 51.5 ms)
+__global__ void __launch_bounds__(256, 6) k1d_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
                                   uint8_t* dirty, RoundDev* rd) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool upd = false, req = false;
