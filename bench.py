@@ -54,7 +54,7 @@ WORKLOADS = {
                  gen=lambda seed: synth.site_scan(seed=seed, stations=40, rgb=True),
                  sample_gen=lambda seed: synth.site_scan(seed=seed, stations=40,
                                                          station_ids=[0], rgb=False),
-                 k=1, ratio=0.05, sample=400_000, ref_sample=150_000, tune_sample=25_000_000),
+                 k=1, ratio=0.05, sample=400_000, ref_sample=150_000, tune_sample=100_000_000),
     "site4": dict(desc="merged site scan, 4 stations x 10000x2500 rays (100M points) of the "
                        "200x200x30 m site generator, int32 mm; k=1; keep 5%",
                   gen=lambda seed: synth.site_scan(seed=seed, station_ids=[0, 1, 2, 3], rgb=False),
@@ -211,7 +211,7 @@ ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop:
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a one-station
 # site scan at the leaf capacity below; reported only while the kNN sources
 # hash to src_sha and the timed run uses the same leaf capacity and k.
-KNN_TRAFFIC = {"k": 1, "leaf_max": 0, "bytes_per_query": None, "src_sha": ""}
+KNN_TRAFFIC = {"k": 1, "leaf_max": 32, "bytes_per_query": 113.9, "src_sha": "c685e3be5fa90ce5"}
 KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
                "paper_2311_17604_gb300/csrc/pd_kernels.h"]
 
@@ -250,9 +250,11 @@ def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
     knn_ach = gbs((q1 + rq) * bq, ms_knn)
     sha = knn_src_sha()
     tr = KNN_TRAFFIC
-    traffic = (tr["bytes_per_query"] * (q1 + rq)
-               if tr["bytes_per_query"] and tr["src_sha"] == sha and tr["leaf_max"] == leaf
-               and tr["k"] == k else None)
+    # DRAM bytes of the first pass (one launch), from the capture scaled by the
+    # queries; the re-searches have no capture of their own at this size
+    traffic1 = (tr["bytes_per_query"] * q1
+                if tr["bytes_per_query"] and tr["src_sha"] == sha and tr["leaf_max"] == leaf
+                and tr["k"] == k else None)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     peak_ops = sms * 4 * 32 * mhz * 1e6
@@ -267,9 +269,15 @@ def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
               "total": mean("ms_total")}
     return {"bound": "hbm", "kernel": "knn_kernel: kNN/cost search (first full pass + re-searches)",
             "achieved": knn_ach, "peak": peak, "unit": "GB/s", "frac": knn_ach / peak,
-            "peak_kind": kind, "traffic": traffic,
+            "peak_kind": kind, "traffic": None,
+            "traffic_note": "no single capture covers the first pass and the re-searches; "
+                            "first_pass.traffic is the first pass's (one launch)",
             "units": q1 + rq, "unit_name": "queries", "bytes_per_unit": bq, "ms": ms_knn,
             "first_pass": {"queries": q1, "ms": ms1, "achieved": gbs(q1 * bq, ms1),
+                           "traffic": traffic1,
+                           "traffic_basis": "%s B per query (ncu dram read + write of the "
+                                            "first pass, one-station site scan, leaf %d) x "
+                                            "queries" % (tr["bytes_per_query"], tr["leaf_max"]),
                            "frac": gbs(q1 * bq, ms1) / peak,
                            "pairs_per_query": pairs / max(q1, 1),
                            "alu": {"achieved": alu / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
@@ -289,19 +297,30 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
 
+def _batch_scan(sp):
+    s = synth.room_scan(seed=sp["seed"], n_az=sp["n_az"], n_el=sp["n_el"], dims=sp["dims"],
+                        scanner=sp["scanner"], rgb=True)
+    return s.xyz, s.rgb
+
+
 def run_batched(args, pd, torch, dev, stream):
     """A batch of room scans shaped like the 512-scan workload (sizes
     log-uniform in 50k-5M, room size and scanner from the seed, RGB, colour
     term 0.3, k = 1, keep 5-50 %), bounded to --batch-count scans."""
+    import multiprocessing as mp
+
     import oracle
     specs = synth.batch_specs(seed=0, count=args.batch_count, n_lo=5e4, n_hi=5e6)
     clouds, total = [], 0
-    for sp in specs:
-        s = synth.room_scan(seed=sp["seed"], n_az=sp["n_az"], n_el=sp["n_el"], dims=sp["dims"],
-                            scanner=sp["scanner"], rgb=True)
-        clouds.append({"xyz": torch.from_numpy(s.xyz).to(dev), "rgb": torch.from_numpy(s.rgb).to(dev),
+    # the scans are cast on the host cores (a spawned pool: this process
+    # already holds a CUDA context)
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        scans = pool.map(_batch_scan, specs, chunksize=1)
+    for sp, (xyz, rgb) in zip(specs, scans):
+        clouds.append({"xyz": torch.from_numpy(xyz).to(dev), "rgb": torch.from_numpy(rgb).to(dev),
                        "ratio": sp["ratio"]})
-        total += s.n
+        total += xyz.shape[0]
+    del scans
     ctx = pd.Context()
     kw = dict(k=1, term=pd.PD_TERM_COLOR, weight=0.3)
     big = max(clouds, key=lambda c: int(c["xyz"].shape[0]))
