@@ -218,7 +218,7 @@ struct pd_grid {
     int k1_exact;    // k = 1 density searches: nearest entries that must be exact (0: all 8;
                      //   the rest of the 8 stored are kept below the reported horizon)
     int k1_exact_rq; // ... in the re-searches of the rounds
-    int sparse_rq;   // k = 1 density re-searches over a list of the flagged points, 4 lanes
+    int sparse_rq;   // k = 1 density re-searches over a list of the flagged points, 2 lanes
                      //   each (else a warp per flagged leaf group)
     double compact_at;  // the rounds compact the grid once live < compact_at * built
                         //   (0: the cost's default)
@@ -893,7 +893,7 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
     if (filter == FILT_BELOW_SELF) a.fprim_out = fout;
     if (filter == FILT_BELOW_TAU) a.lam_out = fout;
     if (filter == FILT_NONE && g->sparse_rq && g->rq_list) {
-        // k = 1 density re-searches: the flagged points, listed, 4 lanes each
+        // k = 1 density re-searches: the flagged points, listed, 2 lanes each
         // over their own cells (the weighted and k >= 2 rounds re-search few
         // points per round, where a warp per flagged group measured faster)
         ArenaUse au;

@@ -605,19 +605,20 @@ __global__ void __launch_bounds__(PD_WARPS * 32, (S == 8 && !W && !LIST) ? 8 : 1
 }
 
 // Sparse re-searches: the listed queries (Morton positions, list[0 .. *count))
-// run 8 to a warp, 4 lanes per query, each query over the 3x3x3 cells of its
-// own leaf level.  The 4 lanes of a query resolve its 27 cells (every 4th
-// one) into shared memory; a coarse leaf reached from two cells is kept once.
-// Each lane then walks the staged ranges on its own, taking positions
-// b + sub, b + sub + 4, ... of every range whose box is not beyond its own
-// partial bound (never closer than the merged one; the smallest box distance
-// it skipped bounds the reported horizon), and keeps a partial list; the 4
-// partial lists merge once per level.  Lists are packed (one 64-bit key per
-// entry, 32-bit distances) when every range of the warp's level lies within
-// 3 cells of 2^13 mm.  Used for the re-searches of the removal rounds, where
-// the flagged queries are few per leaf group and a warp per group would idle
-// most lanes.
-#define SP_LANES 4
+// run SP_SLOTS to a warp, SP_LANES lanes per query, each query over the
+// 3x3x3 cells of its own leaf level.  The lanes of a query resolve its 27
+// cells (every SP_LANES-th one) into shared memory; a coarse leaf reached
+// from two cells is kept once.  Each lane then walks the staged ranges on its
+// own, taking positions b + sub, b + sub + SP_LANES, ... of every range whose
+// box is not beyond its own partial bound (never closer than the merged one;
+// the smallest box distance it skipped bounds the reported horizon), and
+// keeps a partial list; the partial lists merge once per level.  Lists are
+// packed (one 64-bit key per entry, 32-bit distances) when every range of the
+// warp's level lies within 3 cells of 2^13 mm.  Used for the re-searches of
+// the removal rounds, where the flagged queries are few per leaf group and a
+// warp per group would idle most lanes.  2 lanes per query (16 queries per
+// warp) measured faster than 4 or 8 and level with 1.
+#define SP_LANES 2
 #define SP_SLOTS (32 / SP_LANES)
 
 template <int S, bool W, class TL, bool PACK>
@@ -726,8 +727,8 @@ __global__ void __launch_bounds__(PD_WARPS * 32) knn_sparse_kernel(GridView g, K
                 cy = (int)compact3(c0 >> (3 * L + 1));
                 cz = (int)compact3(c0 >> (3 * L + 2));
             }
-            // resolve the 27 cells into shared memory, the 4 lanes of a query
-            // taking every 4th one
+            // resolve the 27 cells into shared memory, the lanes of a query
+            // taking every SP_LANES-th one
             bool small = true;  // every range of this lane within 3 cells of 2^13 mm
             if (todo) {
                 const int lim = 1 << (g.B - L);  // todo lanes have L < B or L == B

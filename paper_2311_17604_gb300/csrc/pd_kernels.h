@@ -145,7 +145,7 @@ cudaError_t launch_knn_flagged(const GridView& g, const KnnArgs& a, int* glist, 
                                cudaStream_t st);
 cudaError_t launch_knn(const GridView& g, const KnnArgs& a, cudaStream_t st);
 // Full (FILT_NONE) searches of the listed Morton positions list[0 .. *count)
-// (count on the device, at most cap), 4 lanes per query, each over its own
+// (count on the device, at most cap), 2 lanes per query, each over its own
 // leaf cells: for sparse re-searches.
 cudaError_t launch_knn_sparse(const GridView& g, const KnnArgs& a, const int* list,
                               const int* count, int64_t cap, cudaStream_t st);
