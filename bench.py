@@ -304,9 +304,11 @@ def _batch_scan(sp):
 
 
 def run_batched(args, pd, torch, dev, stream):
-    """A batch of room scans shaped like the 512-scan workload (sizes
-    log-uniform in 50k-5M, room size and scanner from the seed, RGB, colour
-    term 0.3, k = 1, keep 5-50 %), bounded to --batch-count scans."""
+    """The batched workload: --batch-count room scans (sizes log-uniform in
+    50k-5M, room size and scanner from the seed, RGB, colour term 0.3, k = 1,
+    keep 5-50 %) decimated as one packed grid (PD_BATCH_PACKED).  The first
+    --batch-compare scans also run through concurrent slots and one at a time
+    through the single-scan path, for the comparison."""
     import multiprocessing as mp
 
     import oracle
@@ -315,47 +317,69 @@ def run_batched(args, pd, torch, dev, stream):
     # the scans are cast on the host cores (a spawned pool: this process
     # already holds a CUDA context)
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
-        scans = pool.map(_batch_scan, specs, chunksize=1)
-    for sp, (xyz, rgb) in zip(specs, scans):
-        clouds.append({"xyz": torch.from_numpy(xyz).to(dev), "rgb": torch.from_numpy(rgb).to(dev),
-                       "ratio": sp["ratio"]})
-        total += xyz.shape[0]
-    del scans
+        for sp, (xyz, rgb) in zip(specs, pool.imap(_batch_scan, specs, chunksize=1)):
+            clouds.append({"xyz": torch.from_numpy(xyz).to(dev),
+                           "rgb": torch.from_numpy(rgb).to(dev), "ratio": sp["ratio"]})
+            total += xyz.shape[0]
     ctx = pd.Context()
     kw = dict(k=1, term=pd.PD_TERM_COLOR, weight=0.3)
     big = max(clouds, key=lambda c: int(c["xyz"].shape[0]))
     leaf = args.leaf_max or pd.pd_autotune(ctx, big["xyz"], big["ratio"], rgb=big["rgb"],
                                            sample=1_000_000, stream=stream, **kw)
-    pd.pd_decimate_batch(ctx, clouds[:4], concurrency=4, stream=stream, **kw)   # warm
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    keeps, stats = pd.pd_decimate_batch(ctx, clouds, concurrency=args.batch_slots,
-                                        stream=stream, **kw)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    pd.pd_decimate_batch(ctx, clouds[:8], stream=stream, **kw)   # warm (packed)
+    l0 = pd.lib().pd__launch_count()
+    (keeps, stats), packed_ms = timed(lambda: pd.pd_decimate_batch(
+        ctx, clouds, concurrency=pd.PD_BATCH_PACKED, stream=stream, **kw))
+    launches = pd.lib().pd__launch_count() - l0
     for c, kp in zip(clouds, keeps):
         assert int(kp.sum().item()) == oracle.target_count(int(c["xyz"].shape[0]), c["ratio"])
-    # the same scans one at a time through the single-scan path
-    e0.record(stream)
-    for c in clouds:
-        g = pd.Grid(ctx, c["xyz"], rgb=c["rgb"], stream=stream)
-        pd.pd_decimate_ratio(g, c["ratio"], stream=stream, **kw)
-        g.free()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    single_ms = e0.elapsed_time(e1)
-    per_scan = [st["ms_total"] for st in stats]
+    del keeps
+    # the comparison: the first scans through slots and one at a time
+    sub = clouds[:args.batch_compare]
+    sub_pts = sum(int(c["xyz"].shape[0]) for c in sub)
+    pd.pd_decimate_batch(ctx, sub[:4], concurrency=4, stream=stream, **kw)   # warm (slots)
+    (_, sstats), slots_ms = timed(lambda: pd.pd_decimate_batch(
+        ctx, sub, concurrency=args.batch_slots, stream=stream, **kw))
+    (_, pstats), psub_ms = timed(lambda: pd.pd_decimate_batch(
+        ctx, sub, concurrency=pd.PD_BATCH_PACKED, stream=stream, **kw))
+
+    def single():
+        for c in sub:
+            g = pd.Grid(ctx, c["xyz"], rgb=c["rgb"], stream=stream)
+            pd.pd_decimate_ratio(g, c["ratio"], stream=stream, **kw)
+            g.free()
+    _, single_ms = timed(single)
+    per_scan = [st["ms_total"] for st in sstats]
     ctx.close()
     return {"workload": "%d room scans, sizes log-uniform 50k-5M (%d points), RGB, k=1 + 0.3 x "
                         "colour term, keep U[5%%, 50%%]" % (len(clouds), total),
-            "scans": len(clouds), "points": total, "slots": args.batch_slots, "leaf_max": leaf,
-            "value": total / (batch_ms / 1e3), "unit": UNIT, "ms": batch_ms,
-            "single_scan_loop": {"value": total / (single_ms / 1e3), "ms": single_ms},
-            "speedup_vs_single": single_ms / batch_ms,
-            "per_scan_ms": {"p50": _pct(per_scan, 50), "p99": _pct(per_scan, 99),
-                            "what": "each scan's decimation time on its slot's stream"}}
+            "mode": "packed: every scan in one grid, one launch per round kernel for all scans",
+            "scans": len(clouds), "points": total, "leaf_max": leaf,
+            "value": total / (packed_ms / 1e3), "unit": UNIT, "ms": packed_ms,
+            "rounds": stats[0]["rounds"], "gpu_launches": int(launches),
+            "per_scan_ms": {"p50": packed_ms, "p99": packed_ms,
+                            "what": "every scan of a packed batch finishes with the batch"},
+            "compare": {"scans": len(sub), "points": sub_pts,
+                        "packed": {"value": sub_pts / (psub_ms / 1e3), "ms": psub_ms},
+                        "slots": {"value": sub_pts / (slots_ms / 1e3), "ms": slots_ms,
+                                  "slots": args.batch_slots,
+                                  "per_scan_ms": {"p50": _pct(per_scan, 50),
+                                                  "p99": _pct(per_scan, 99),
+                                                  "what": "each scan's decimation time on its "
+                                                          "slot's stream"}},
+                        "single_scan_loop": {"value": sub_pts / (single_ms / 1e3),
+                                             "ms": single_ms},
+                        "packed_vs_single": single_ms / psub_ms}}
 
 
 def run_serving(args, pd, torch, dev):
@@ -639,7 +663,9 @@ def main(argv=None):
                          "it live in pinned host memory (0: no budget)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--batch-count", type=int, default=48)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-compare", type=int, default=48,
+                    help="scans of the batch also run through slots and one at a time")
     ap.add_argument("--batch-slots", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=50.0)

@@ -252,15 +252,41 @@ int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_ho
                      uint8_t* keep_host, void* stream, pd_stats* stats /* may be NULL */);
 
 /*
- * Batch of independent scans (many clouds of uneven size).  Scans run through
- * `concurrency` slots (0 = 8); each slot has its own stream and host thread
- * and runs pd_build_grid + pd_decimate_count on its scans, so the slots'
- * kernels overlap on the device.  Every scan gets the same result it gets
- * alone.  The work is ordered after what is queued on `stream`, and `stream`
- * waits for all of it; the call returns when every scan is done.
+ * Batch of independent scans (many clouds of uneven size; the sequential
+ * greedy of section "Sub-sampling algorithm" applied to each scan on its own,
+ * with its own target m or floor(ratio * n)).
+ *
+ * concurrency == PD_BATCH_PACKED: every scan is moved (a copy; the caller's
+ * buffers are only read) into its own aligned tile of one packed cloud, and
+ * the whole batch is decimated as ONE grid: one grid build, one first
+ * neighbour pass, and one sequence of removal rounds whose every launch
+ * covers all scans.  The tiles are at least 2^T - E apart (E the largest
+ * per-axis extent of any scan, 2^T >= 3E + 2), farther than any two points
+ * of one scan, so no search leaves its scan; only the removal threshold of a
+ * round is selected per scan.  For the density cost each scan gets exactly
+ * its stand-alone result (the sequential greedy's retained set).  With a
+ * colour or orientation term the rounds of the batch differ from those of a
+ * scan alone, so the result is the same within the tolerance those terms
+ * have alone.  A scan's stats are those of the whole batch, with its own n
+ * and m.  Extra device memory: the packed copy (16 B per point, 19 with
+ * colours, 28 with normals) and one grid over all points.  A batch that
+ * cannot be packed falls back to 8 slots (below): more than PD_BATCH_MAX_SCANS
+ * scans or 2^31 - 64 points, a target of k points or fewer, a missing colour
+ * or normal array, tiles beyond the coordinate range (2^25 mm), or a scan
+ * with more coincident points than it must lose.
+ *
+ * concurrency >= 0: scans run through `concurrency` slots (0 = 8); each slot
+ * has its own stream and host thread and runs pd_build_grid +
+ * pd_decimate_count on its scans, so the slots' kernels overlap on the
+ * device.  Every scan gets the same result it gets alone.
+ *
+ * The work is ordered after what is queued on `stream`, and `stream` waits
+ * for all of it; the call returns when every scan is done.
  * Returns PD_OK, or the first error of any scan (each scan's own status is in
  * its descriptor).
  */
+#define PD_BATCH_PACKED (-1)
+#define PD_BATCH_MAX_SCANS 4096
 typedef struct {
     const int32_t* xyz_dev;    /* n x 3 int32, device */
     const uint8_t* rgb_dev;    /* n x 3 uint8, device, or NULL */

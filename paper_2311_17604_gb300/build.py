@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpd.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["grid.cu", "knn.cu", "rounds.cu", "rounds_dev.cu", "capi.cu", "noalloc.cu", "normals.cu",
-           "serve.cu", "quality.cu", "wup.cu"]
+SOURCES = ["grid.cu", "knn.cu", "rounds.cu", "rounds_dev.cu", "capi.cu", "batch.cu", "noalloc.cu",
+           "normals.cu", "serve.cu", "quality.cu", "wup.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

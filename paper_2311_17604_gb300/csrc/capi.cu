@@ -228,6 +228,12 @@ struct pd_grid {
     size_t arena_cap;
     int trace;       // PD_TRACE set: one line per removal round on stderr
     int max_rounds;  // PD_MAX_ROUNDS: diagnostic stop (0 = none)
+    // packed batch (pd_decimate_batch): nseg scans in tiles of edge
+    // 2^seg_shift mm; per-scan targets and grid ranges in seg (device)
+    int nseg = 0, seg_shift = 0;
+    SegDev* seg = nullptr;
+    int* seg_chunk0 = nullptr;
+    std::vector<long long> seg_n, seg_m;  // host copies: points and targets per scan
 };
 
 namespace {
@@ -456,7 +462,7 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
                     g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64, g->glist,
-                    g->gcount, g->cmin, g->nbr0};
+                    g->gcount, g->cmin, g->nbr0, g->seg, g->seg_chunk0};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -913,21 +919,35 @@ int knn_flag(pd_grid* g, const pd_cost_params* cp, int filter, int S, const uint
 // A round the device could not settle: the danger analysis overflowed (or
 // fewer than k low points exist), or the fixpoint needed more sweeps.
 int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint8_t* rej,
-                 int* dep,
-                 int* cand, int2* pairs, int pair_cap, int64_t* removed) {
+                 int* dep, int* cand, int2* pairs, int pair_cap, SelBuffers* sel,
+                 uint32_t* seg_hist, int64_t* removed) {
     int* d = g->d_int;
     if (h.overflow) {
         // drop this round's candidates and remove the global maximum only
         CK(launch_remove(cand, &rd->ncand, 0, inP, rej, g->alive, g->d_u64, g->st));
         CK(cudaMemsetAsync(inP, 0, g->ng, g->st));
         CK(cudaMemsetAsync(rej, 0, g->ng, g->st));
-        Sel top;
-        int rc = select_rank(g, g->prim, g->alive, 1, 0, &top, nullptr);
-        if (rc) return rc;
         CK(cudaMemsetAsync(d + 4, 0, sizeof(int), g->st));
-        CK(launch_accept_above(g->prim, g->pos, g->alive, g->ng, top.prim, top.idx, inP, cand,
-                               d + 4, g->st));
-        CK(launch_remove(cand, d + 4, 1, inP, rej, g->alive, g->d_u64, g->st));
+        if (g->nseg) {
+            // packed batch: the largest key of every scan still above its
+            // target (each is its scan's next sequential pop)
+            int one = 1, zero = 0;
+            CK(cudaMemcpyAsync(&rd->seg_rank_one, &one, sizeof(int), cudaMemcpyHostToDevice,
+                               g->st));
+            CK(seg_launch_select(g->prim, g->pos, g->alive, g->ng, *sel, seg_hist, rd, g->seg,
+                                 g->seg_chunk0, g->nseg, g->st));
+            CK(cudaMemcpyAsync(&rd->seg_rank_one, &zero, sizeof(int), cudaMemcpyHostToDevice,
+                               g->st));
+            CK(seg_launch_accept(g->prim, g->pos, g->alive, g->ng, rd, inP, cand, d + 4, g->st));
+            CK(launch_remove(cand, d + 4, g->nseg, inP, rej, g->alive, g->d_u64, g->st));
+        } else {
+            Sel top;
+            int rc = select_rank(g, g->prim, g->alive, 1, 0, &top, nullptr);
+            if (rc) return rc;
+            CK(launch_accept_above(g->prim, g->pos, g->alive, g->ng, top.prim, top.idx, inP, cand,
+                                   d + 4, g->st));
+            CK(launch_remove(cand, d + 4, 1, inP, rej, g->alive, g->d_u64, g->st));
+        }
     } else {
         // keep sweeping the fixpoint until nothing changes
         for (int it = 0; it < 1000000; it++) {
@@ -952,9 +972,16 @@ int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint
     return PD_OK;
 }
 
+static_assert(PD_BATCH_MAX_SCANS == PD_SEG_MAX, "packed batch scan limit");
+
+// A packed batch one of whose scans has more coincident points than it must
+// lose: the batch runs its scans one grid each instead.
+#define PD_SEG_FALLBACK 100
+
 // Duplicate phase: coincident points beyond the smallest index of their
 // class are the first pops of the sequential greedy (their cost is +inf).
-int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
+int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed,
+                      const std::vector<long long>* seg_need = nullptr) {
     *removed = 0;
     Temps tmp(g);
     uint8_t* dup;
@@ -963,6 +990,22 @@ int remove_duplicates(pd_grid* g, int64_t need, int64_t* removed) {
     unsigned long long nd = 0;
     CK(cudaMemcpyAsync(&nd, g->d_u64, sizeof(nd), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
+    if (g->nseg && nd > 0) {
+        // packed batch: every scan must be able to lose all its duplicates
+        unsigned long long* cnt;
+        TALLOC(tmp, cnt, unsigned long long, g->nseg);
+        CK(cudaMemsetAsync(cnt, 0, g->nseg * sizeof(*cnt), g->st));
+        CK(seg_launch_count(dup, g->pos, g->ng, g->seg_shift, cnt, g->st));
+        std::vector<unsigned long long> hc(g->nseg);
+        CK(cudaMemcpyAsync(hc.data(), cnt, g->nseg * sizeof(*cnt), cudaMemcpyDeviceToHost,
+                           g->st));
+        CK(cudaStreamSynchronize(g->st));
+        for (int i = 0; i < g->nseg; i++)
+            if ((long long)hc[i] > (*seg_need)[i]) return PD_SEG_FALLBACK;
+        *removed = (int64_t)nd;
+        CK(launch_dup_remove(dup, g->pos, g->ng, 0, g->alive, g->st));
+        return PD_OK;
+    }
     int idx_min = 0;
     if (nd > 0 && need > 0) {
         if ((int64_t)nd > need) {
@@ -1078,7 +1121,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     int64_t live = g->n;
     // ---- duplicate phase
     int64_t nd = 0;
-    rc = remove_duplicates(g, live - m, &nd);
+    std::vector<long long> seg_need;
+    for (int i = 0; i < g->nseg; i++) seg_need.push_back(g->seg_n[i] - g->seg_m[i]);
+    rc = remove_duplicates(g, live - m, &nd, g->nseg ? &seg_need : nullptr);
     if (rc) return rc;
     g->stats.dup_removed = nd;
     live -= nd;
@@ -1086,6 +1131,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
         rc = compact_rebuild(g, false);
         if (rc) return rc;
     }
+    // packed batch: every scan's grid range and its selection work items
+    if (g->nseg)
+        CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->nseg, g->seg_shift, g->st));
     // ---- first neighbour pass
     {
         unsigned long long* dpairs;
@@ -1161,8 +1209,19 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     CK(cudaMemsetAsync(sb.hist, 0, 4096 * sizeof(uint32_t), g->st));
     RoundDev* rd;
     RALLOC(rd, RoundDev, 1);
+    uint32_t* seg_hist = nullptr;  // packed batch: a 4096-bin histogram per scan
+    if (g->nseg) {
+        RALLOC(seg_hist, uint32_t, (size_t)g->nseg * 4096);
+        CK(cudaMemsetAsync(seg_hist, 0, (size_t)g->nseg * 4096 * sizeof(uint32_t), g->st));
+    }
     RoundDev h;
     memset(&h, 0, sizeof(h));
+    if (g->nseg) {
+        h.seg = g->seg;
+        h.seg_chunk0 = g->seg_chunk0;
+        h.nseg = g->nseg;
+        h.seg_shift = g->seg_shift;
+    }
     h.live = live;
     h.m = m;
     h.band = band_max;
@@ -1176,8 +1235,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     int64_t built = live;
     // small clouds are bound by launches: from the third round on, a round's
     // launches are captured into a CUDA graph and replayed (PD_ROUND_GRAPH:
-    // 1 always, 0 never; default for grids up to 8M points)
-    bool round_graph = g->n <= ((int64_t)8 << 20);
+    // 1 always, 0 never; default for grids up to 8M points and packed batches)
+    bool round_graph = g->n <= ((int64_t)8 << 20) || g->nseg > 0;
     if (getenv("PD_ROUND_GRAPH")) round_graph = atoi(getenv("PD_ROUND_GRAPH")) != 0;
     void* graph_pos = nullptr;
     long long graph_kernels = 0;
@@ -1191,7 +1250,11 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             CK(round_launch_setup(rd, g->st));
             {
                 Span t(T, &g->stats.ms_select);
-                CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
+                if (g->nseg)
+                    CK(seg_launch_select(g->prim, g->pos, g->alive, g->ng, sb, seg_hist, rd,
+                                         g->seg, g->seg_chunk0, g->nseg, g->st));
+                else
+                    CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
             }
             if (g->density_k1) {
                 CK(round_launch_k1(v, g->prim, g->alive, g->nbr, g->nbr0, g->flg, g->rk2, g->ng, S,
@@ -1309,7 +1372,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             // settle on the host: finish the fixpoint, or (danger overflow / too
             // few low points) take only the global maximum, always removable
             int64_t removed = 0;
-            rc = settle_round(g, rd, h, inP, rej, dep, cand, pairs, pair_cap, &removed);
+            rc = settle_round(g, rd, h, inP, rej, dep, cand, pairs, pair_cap, &sb, seg_hist,
+                              &removed);
             if (rc) return rc;
             if (g->density_k1)
                 CK(round_launch_k1_update(bufview(g, cp), g->alive, g->ng, S, dirty, rd, g->st));
@@ -1361,6 +1425,9 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             Span t(T, &g->stats.ms_build);
             rc = compact_rebuild(g, true);
             if (rc) return rc;
+            if (g->nseg)
+                CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->nseg, g->seg_shift,
+                                     g->st));
             built = live;
         }
     }
@@ -1980,7 +2047,157 @@ extern "C" int pd_quality_report(pd_ctx* ctx, const int32_t* xyz_dev, const uint
 }
 
 // ============================================================ API: batch
-// Many independent scans through a fixed number of concurrent slots: every
+namespace {
+
+// Every scan of a batch in one grid (the packed mode of pd_decimate_batch):
+// scan i moves into the aligned tile of edge 2^T mm whose Morton index is i,
+// the tiles are decimated together, and the keep masks are copied back.
+// Returns PD_SEG_FALLBACK when the batch cannot be packed (then nothing was
+// written): too many scans or points, a target of k points or fewer (a scan
+// must keep more than k, so that every search stays inside it), a missing
+// colour or normal array, a tile arrangement beyond the coordinate range, or
+// a scan with more coincident points than it must lose.
+int batch_packed(pd_ctx* ctx, pd_scan_desc* scans, int nscans, const pd_cost_params* cp,
+                 cudaStream_t st) {
+    if (nscans > PD_SEG_MAX || !cp || cp->k < 1 || cp->k > PD_KMAX) return PD_SEG_FALLBACK;
+    const bool want_rgb = cp->term == PD_TERM_COLOR, want_nrm = cp->term == PD_TERM_ORIENT;
+    std::vector<PackScan> hs(nscans);
+    std::vector<long long> nv(nscans), mv(nscans);
+    long long N = 0, M = 0;
+    int nchunks = 0;
+    for (int i = 0; i < nscans; i++) {
+        const pd_scan_desc& d = scans[i];
+        const long long m = d.m >= 0 ? d.m : (long long)(d.ratio * (double)d.n);
+        if (m <= cp->k || (want_rgb && !d.rgb_dev) || (want_nrm && !d.normals_dev))
+            return PD_SEG_FALLBACK;
+        PackScan& p = hs[i];
+        memset(&p, 0, sizeof(p));
+        p.xyz = d.xyz_dev;
+        p.rgb = want_rgb ? d.rgb_dev : nullptr;
+        p.nrm = want_nrm ? d.normals_dev : nullptr;
+        p.keep = d.keep_dev;
+        p.n = d.n;
+        p.off = N;
+        p.chunk0 = nchunks;
+        for (int a = 0; a < 3; a++) {
+            p.bb[a] = 0x7fffffff;
+            p.bb[3 + a] = (int)0x80000000;
+        }
+        nv[i] = d.n;
+        mv[i] = m;
+        N += d.n;
+        M += m;
+        nchunks += (int)((d.n + PD_SEG_CHUNK - 1) / PD_SEG_CHUNK);
+        if (N >= (1ll << 31) - 64) return PD_SEG_FALLBACK;
+    }
+    struct Blocks {  // released in order on every exit path
+        pd_ctx* c;
+        cudaStream_t st;
+        std::vector<void*> p;
+        void* get(size_t b) {
+            void* x = ctx_alloc(c, b, st);
+            if (x) p.push_back(x);
+            return x;
+        }
+        ~Blocks() {
+            for (void* x : p) ctx_free(c, x, st);
+        }
+    } blk{ctx, st, {}};
+    PackScan* ds = (PackScan*)blk.get(sizeof(PackScan) * nscans);
+    if (!ds) return PD_ENOMEM;
+    if (cudaMemcpyAsync(ds, hs.data(), sizeof(PackScan) * nscans, cudaMemcpyHostToDevice, st) ||
+        pack_launch_bbox(ds, nscans, nchunks, st) ||
+        cudaMemcpyAsync(hs.data(), ds, sizeof(PackScan) * nscans, cudaMemcpyDeviceToHost, st) ||
+        cudaStreamSynchronize(st)) {
+        set_err(ctx, "pd_decimate_batch: packing failed%s", "", 0);
+        return PD_ECUDA;
+    }
+    // tile edge 2^T >= 3 E + 2, E the largest per-axis extent of any scan: two
+    // points of different tiles are at least 2^T - E > sqrt(3) E apart, more
+    // than any two points of one scan, so a scan that keeps more than k points
+    // never finds a neighbour elsewhere
+    long long E = 0;
+    for (const PackScan& p : hs)
+        for (int a = 0; a < 3; a++) E = std::max(E, (long long)p.bb[3 + a] - p.bb[a]);
+    int T = 10;
+    while ((1ll << T) < 3 * E + 2) T++;
+    int td = 1;  // tiles per axis
+    while ((long long)td * td * td < nscans) td *= 2;
+    if ((long long)(td - 1) * (1ll << T) + E >= (1ll << 25)) return PD_SEG_FALLBACK;
+    for (int i = 0; i < nscans; i++) {
+        PackScan& p = hs[i];
+        const long long tile[3] = {(long long)compact3((u64)i), (long long)compact3((u64)i >> 1),
+                                   (long long)compact3((u64)i >> 2)};
+        int* o[3] = {&p.ox, &p.oy, &p.oz};
+        for (int a = 0; a < 3; a++) {
+            const long long v = (tile[a] << T) - (long long)p.bb[a];
+            if (v > 0x7fffffffll || v < -0x7fffffffll) return PD_SEG_FALLBACK;
+            *o[a] = (int)v;
+        }
+    }
+    int32_t* xyz = (int32_t*)blk.get((size_t)N * 12);
+    uint8_t* rgb = want_rgb ? (uint8_t*)blk.get((size_t)N * 3) : nullptr;
+    float* nrm = want_nrm ? (float*)blk.get((size_t)N * 12) : nullptr;
+    uint8_t* keep = (uint8_t*)blk.get((size_t)N);
+    if (!xyz || !keep || (want_rgb && !rgb) || (want_nrm && !nrm)) {
+        set_err(ctx, "pd_decimate_batch: allocation of the packed batch failed%s (%lld points)",
+                "", N);
+        return PD_ENOMEM;
+    }
+    if (cudaMemcpyAsync(ds, hs.data(), sizeof(PackScan) * nscans, cudaMemcpyHostToDevice, st) ||
+        pack_launch_copy(ds, nscans, nchunks, xyz, rgb, nrm, st)) {
+        set_err(ctx, "pd_decimate_batch: packing failed%s", "", 0);
+        return PD_ECUDA;
+    }
+    pd_grid* g = nullptr;
+    int rc = pd_build_grid(ctx, xyz, rgb, N, nullptr, st, &g);
+    if (rc) return rc;
+    struct GridGuard {
+        pd_grid* g;
+        ~GridGuard() {
+            if (g) pd_grid_free(g);
+        }
+    } gg{g};
+    g->nseg = nscans;
+    g->seg_shift = T;
+    g->seg_n = nv;
+    g->seg_m = mv;
+    g->seg = (SegDev*)ctx_alloc(ctx, sizeof(SegDev) * nscans, st);
+    g->seg_chunk0 = (int*)ctx_alloc(ctx, sizeof(int) * (nscans + 1), st);
+    if (!g->seg || !g->seg_chunk0) {
+        set_err(ctx, "pd_decimate_batch: allocation of the scan table failed%s", "", 0);
+        return PD_ENOMEM;
+    }
+    std::vector<SegDev> sd(nscans);
+    memset(sd.data(), 0, sizeof(SegDev) * nscans);
+    for (int i = 0; i < nscans; i++) {
+        sd[i].m = mv[i];
+        sd[i].done = 1;
+    }
+    if (cudaMemcpyAsync(g->seg, sd.data(), sizeof(SegDev) * nscans, cudaMemcpyHostToDevice, st))
+        return PD_ECUDA;
+    pd_cost_params c2 = *cp;
+    c2.normals_dev = nrm;
+    rc = pd_decimate_count(g, &c2, M, keep, st);
+    if (rc) return rc;
+    if (pack_launch_unpack(ds, nscans, nchunks, keep, st)) return PD_ECUDA;
+    pd_stats gs;
+    pd_grid_stats(g, &gs);
+    for (int i = 0; i < nscans; i++) {
+        scans[i].stats = gs;  // the whole batch's decimation
+        scans[i].stats.n = nv[i];
+        scans[i].stats.m = mv[i];
+        scans[i].status = PD_OK;
+    }
+    if (cudaStreamSynchronize(st)) return PD_ECUDA;
+    return PD_OK;
+}
+
+}  // namespace
+
+// Many independent scans.  Packed mode (concurrency PD_BATCH_PACKED): all
+// scans in one grid, decimated together (batch_packed).  Otherwise, or when
+// a batch cannot be packed, a fixed number of concurrent slots: every
 // slot owns a CUDA stream and a host thread that builds the scan's grid and
 // runs its removal rounds; the slots' kernels overlap on the device.  The
 // call orders all work after what is already queued on `stream` and makes
@@ -1997,11 +2214,16 @@ extern "C" int pd_decimate_batch(pd_ctx* ctx, pd_scan_desc* scans, int nscans,
             return PD_EINVAL;
         }
     }
+    cudaStream_t caller = (cudaStream_t)stream;
+    if (concurrency == PD_BATCH_PACKED) {
+        int rc = batch_packed(ctx, scans, nscans, cp, caller);
+        if (rc != PD_SEG_FALLBACK) return rc;
+        concurrency = 0;  // not packable: slots
+    }
     int slots = concurrency > 0 ? concurrency : 8;
     if (slots > nscans) slots = nscans;
     int dev = 0;
     if (cudaGetDevice(&dev)) return PD_ECUDA;
-    cudaStream_t caller = (cudaStream_t)stream;
     cudaEvent_t start;
     if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) return PD_ECUDA;
     cudaEventRecord(start, caller);

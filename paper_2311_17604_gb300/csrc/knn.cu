@@ -508,8 +508,17 @@ __device__ __forceinline__ void knn_group(const GridView& g, const KnnArgs& a, i
         tp = a.prim[q];
         ti = qp.w;
     } else if (FILT == FILT_BELOW_TAU) {
-        tp = a.rd ? a.rd->tau_prim : a.tau_prim;
-        ti = a.rd ? a.rd->tau_idx : a.tau_idx;
+        if (a.rd && a.rd->seg) {
+            // packed batch: the threshold of the query's own scan (its
+            // neighbours are all in that scan)
+            if (q >= 0) round_tau(a.rd, qp, tp, ti);
+        } else if (a.rd) {
+            tp = a.rd->tau_prim;
+            ti = a.rd->tau_idx;
+        } else {
+            tp = a.tau_prim;
+            ti = a.tau_idx;
+        }
     }
     // the largest threshold of the warp's queries (chunk skipping); reduced
     // over all 32 lanes so that every lane holds the same value: the skip in

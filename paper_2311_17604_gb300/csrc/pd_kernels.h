@@ -65,6 +65,24 @@ cudaError_t launch_take_xyz(const int* list, const int* count, int64_t cap, cons
 #define PD_FIX_ITERS 32    // device fixpoint sweeps of a k = 1 round (the most)
 #define PD_FIX_ITERS_KK 8  // ... of a k >= 2 round (danger pairs)
 
+// ---------------------------------------------------------------- packed batches
+// Many independent scans decimated in one grid (batch.cu).  Scan i is moved
+// into the aligned cube ("tile") of edge 2^shift mm whose Morton index is i;
+// tiles are far enough apart that no neighbour search reaches another scan,
+// and every scan occupies one contiguous range of the Morton order.  The
+// removal threshold of a round (R2) is selected per scan.
+#define PD_SEG_MAX 4096      // scans of one packed batch (16 tiles per axis)
+#define PD_SEG_CHUNK 8192    // grid positions per work item of the per-scan passes
+struct SegDev {
+    long long live, m, need, rank;
+    unsigned long long tau_prim;  // this round's threshold (~0: nothing to remove)
+    int tau_idx;
+    int done;                     // selection finished for this round
+    unsigned pre[8];
+    int len[2];                   // selection lists: [b, b + len) of the ping-pong buffers
+    int b, e;                     // the scan's grid positions [b, e)
+};
+
 // Per-round control block in device memory (read by the host once per round).
 struct RoundDev {
     long long live, m, need, rank;
@@ -83,7 +101,33 @@ struct RoundDev {
     int density_k1;
     int band_mode;  // 0: shrink on overflow only; 1: also on poor yield
     int fix_iters;  // device fixpoint sweeps per round (<= PD_FIX_ITERS)
+    // packed batch (NULL seg: one scan).  Then tau_prim above is the least
+    // threshold over the scans (a prefilter) and each point takes its own
+    // scan's threshold.
+    SegDev* seg;
+    const int* seg_chunk0;  // nseg + 1 prefix counts of PD_SEG_CHUNK work items
+    int nseg, seg_shift;
+    int seg_rank_one;       // select each scan's largest key only (host settle)
 };
+
+#ifdef __CUDACC__
+// The scan of a packed batch that holds grid point p (its tile's Morton index).
+__device__ __forceinline__ int seg_of(int4 p, int shift) {
+    return (int)morton3((uint32_t)p.x >> shift, (uint32_t)p.y >> shift, (uint32_t)p.z >> shift);
+}
+// The removal threshold of the round that applies to grid point p.
+__device__ __forceinline__ void round_tau(const RoundDev* rd, int4 p, unsigned long long& tp,
+                                          int& ti) {
+    if (rd->seg) {
+        const SegDev& s = rd->seg[seg_of(p, rd->seg_shift)];
+        tp = s.tau_prim;
+        ti = s.tau_idx;
+    } else {
+        tp = rd->tau_prim;
+        ti = rd->tau_idx;
+    }
+}
+#endif
 
 struct SelBuffers {
     u64* p[2];
@@ -264,5 +308,45 @@ cudaError_t wup_launch_exact_tau(const u64* prim, const int4* pos, const uint8_t
 cudaError_t wup_launch_round(const BufView& b, uint8_t* alive, uint8_t* wdirty, int64_t n, int S,
                              int k, RoundDev* rd, u64* mark_p, int* mark_i, uint8_t* pick,
                              cudaStream_t st);
+
+// ---------------------------------------------------------------- batch.cu
+// One scan of a packed batch (device array, host-built): its caller-owned
+// buffers, its first packed position and work item, and the per-axis offset
+// that moves it into its tile (packed = input + o).
+struct PackScan {
+    const int32_t* xyz;
+    const uint8_t* rgb;
+    const float* nrm;
+    uint8_t* keep;
+    long long n, off;
+    int chunk0;
+    int ox, oy, oz;
+    int bb[6];  // bounding box (min x, y, z, max x, y, z), from pack_launch_bbox
+};
+// Bounding boxes of every scan (sc[i].bb, preset to empty boxes by the caller).
+cudaError_t pack_launch_bbox(PackScan* sc, int nsc, int nchunks, cudaStream_t st);
+// Packed coordinates (and colours, normals where out_rgb / out_nrm are set).
+cudaError_t pack_launch_copy(const PackScan* sc, int nsc, int nchunks, int32_t* out_xyz,
+                             uint8_t* out_rgb, float* out_nrm, cudaStream_t st);
+// Every scan's keep mask from the packed one.
+cudaError_t pack_launch_unpack(const PackScan* sc, int nsc, int nchunks, const uint8_t* keep,
+                               cudaStream_t st);
+// Grid ranges [b, e) of every scan and the prefix counts of their work items
+// (chunk0[0..nseg]), from the Morton-ordered positions.
+cudaError_t seg_launch_ranges(const int4* pos, int64_t ng, SegDev* seg, int* chunk0, int nseg,
+                              int shift, cudaStream_t st);
+// Per-scan selection of the round's threshold (R2): every scan's rank-th
+// largest live key, rank from its live count, target and the band.  hist:
+// nseg x 4096 words, zero on entry and on return.
+cudaError_t seg_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t ng,
+                              SelBuffers& b, uint32_t* hist, RoundDev* rd, SegDev* seg,
+                              const int* chunk0, int nseg, cudaStream_t st);
+// cnt[scan] += flagged points of the scan.
+cudaError_t seg_launch_count(const uint8_t* flag, const int4* pos, int64_t ng, int shift,
+                             unsigned long long* cnt, cudaStream_t st);
+// Candidates: every live point whose key reaches its scan's threshold.
+cudaError_t seg_launch_accept(const u64* prim, const int4* pos, const uint8_t* alive, int64_t ng,
+                              const RoundDev* rd, uint8_t* inP, int* cand, int* ncand,
+                              cudaStream_t st);
 
 }  // namespace pd

@@ -234,10 +234,18 @@ __global__ void k1d_cand_kernel(const u64* __restrict__ prim, const int4* __rest
     const uint8_t al = in ? alive[s] : 0;
     const u64 ps = in ? prim[s] : 0;  // loaded beside the alive flag, not after it
     if (al) {
-        const u64 tp = rd->tau_prim;
+        u64 tp = rd->tau_prim;  // packed batch: the least threshold over the scans
         if (ps >= tp) {  // below the threshold on the primary: no index needed
-            const int is = pos[s].w;
-            if (!key_gt(tp, rd->tau_idx, ps, is)) {
+            int ti = rd->tau_idx;
+            int is;
+            if (rd->seg) {  // packed batch: the threshold of the point's own scan
+                const int4 p4 = pos[s];
+                is = p4.w;
+                round_tau(rd, p4, tp, ti);
+            } else {
+                is = pos[s].w;
+            }
+            if (!key_gt(tp, ti, ps, is)) {
                 const uint8_t fl = flg[s];
                 if (fl & 2) {
                     sl = true;
@@ -573,11 +581,12 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
     bool fq = false, lq = false, isc = false, iss = false;
     if (s < n) {
         if (alive[s]) {
-            u64 tp = rd->tau_prim;
-            int ti = rd->tau_idx;
             u64 ps = b.prim[s];
             int4 qs = b.pos[s];
             int is = qs.w;
+            u64 tp;
+            int ti;
+            round_tau(rd, qs, tp, ti);  // packed batch: the threshold of the point's scan
             if (!key_gt(tp, ti, ps, is)) {
                 uint8_t fl = b.flg[s];
                 bool lower = !(fl & 1);

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ERANGE, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EINTERNAL = range(7)
 PD_TERM_NONE, PD_TERM_COLOR, PD_TERM_ORIENT = 0, 1, 2
+PD_BATCH_PACKED = -1      # pd_decimate_batch: every scan in one packed grid
+PD_BATCH_MAX_SCANS = 4096
 PD_KMAX = 16
 PD_STATIC_MAX_POINTS = 65536
 
@@ -453,12 +455,13 @@ def pd_knn_cost_static(xyz, k=1, cost=None, knn=None, stream=None):
     return cost, knn
 
 
-def pd_decimate_batch(ctx: Context, clouds, k=1, term=PD_TERM_NONE, weight=0.0, concurrency=0,
-                      band=0.0, stream=None):
+def pd_decimate_batch(ctx: Context, clouds, k=1, term=PD_TERM_NONE, weight=0.0,
+                      concurrency=PD_BATCH_PACKED, band=0.0, stream=None):
     """Decimate many independent scans; ``clouds`` is a list of dicts with
     ``xyz`` (device int32 [n,3]), ``m`` or ``ratio``, optional ``rgb`` (device
-    uint8 [n,3]) and ``normals`` (device float32 [n,3]).  Returns the keep
-    masks (device uint8) and per-scan stats."""
+    uint8 [n,3]) and ``normals`` (device float32 [n,3]).  ``concurrency``:
+    PD_BATCH_PACKED (all scans in one grid) or a number of concurrent slots
+    (0 = 8).  Returns the keep masks (device uint8) and per-scan stats."""
     torch = _torch()
     descs = (pd_scan_desc * len(clouds))()
     keeps = []
