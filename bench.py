@@ -4,20 +4,23 @@
 A step decimates one synthetic terrestrial-LiDAR scan end to end on the
 device: voxel-grid build (Morton radix sort, octree cell table), the first
 k-nearest-neighbour/cost pass, the removal rounds and the keep mask.  The
-default workload is the 10000 x 2000-ray outdoor scan (ground plane, 40 boxes,
-20 spheres at 1-60 m, 15 % dropout, int32 mm) with the k = 4 density cost,
-keeping 10 % of the points.
+default workload is the merged 40-station site scan (1.0B points, int32 mm +
+RGB, all resident in HBM) with the k = 1 density cost, keeping 5 %.
 
   value   input points / second of device time, inputs resident in HBM
   e2e     the same through pd_decimate_host (host buffers, copies timed)
-  roofline  the first full kNN/cost pass: algorithmic bytes / launch time
+  roofline  the first full kNN/cost pass (the dominant kernel): algorithmic
+            bytes / launch time against the measured copy bandwidth, with the
+            integer-issue roofline that binds it, the whole search, the phases
+            and the whole step beside it
   cpu_baseline  the CPU oracle on a bounded sector of the same scan
-  batched   many room scans of uneven size (sizes log-uniform 50k-5M, RGB,
-            colour term 0.3, keep 5-50 %) through pd_decimate_batch, against
-            the same scans one at a time; per-scan p50/p99 ms
-  serving   Poisson arrivals (50 scans/s) of room scans of 100k-10M points
-            through the pd_serve_* loop with the orientation term and network
-            normals; p50/p99 latency, throughput, normal angular error
+  batched   512 room scans of uneven size (sizes log-uniform 50k-5M, RGB,
+            colour term 0.3, keep 5-50 %) decimated as one packed grid
+            through pd_decimate_batch; the first 48 also through concurrent
+            slots and one at a time
+  serving   Poisson arrivals (50 scans/s) of distinct room scans of 100k-10M
+            points through the pd_serve_* loop with the orientation term and
+            network normals; p50/p99 latency, throughput, normal angular error
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
        python bench.py --impl reference ...   (the CPU oracle as the reference arm)
@@ -234,10 +237,11 @@ def radix_passes(xyz):
 
 def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
     """HBM rooflines from the library's CUDA-event phase timers (on the
-    launching stream) and the algorithmic bytes above.  The dominant kernel of
-    a step is the kNN/cost search (its first full pass plus the re-searches of
-    the removal rounds); the first pass alone, its integer-issue view, the
-    other phases and the whole step are reported beside it."""
+    launching stream) and the algorithmic bytes above.  The top level is the
+    dominant kernel of a step, the first full kNN/cost pass (one launch per
+    step); the whole kNN search (that pass plus the re-searches of the removal
+    rounds), its integer-issue view, the other phases and the whole step are
+    reported beside it."""
     import torch
     mean = lambda key: statistics.mean(s[key] for s in stats)
     peak, kind = measured_peaks()
@@ -248,10 +252,11 @@ def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
     ms_knn = ms1 + msr
     gbs = lambda b, ms: b / (ms / 1e3) / 1e9 if ms > 0 else None
     knn_ach = gbs((q1 + rq) * bq, ms_knn)
+    first_ach = gbs(q1 * bq, ms1)
     sha = knn_src_sha()
     tr = KNN_TRAFFIC
     # DRAM bytes of the first pass (one launch), from the capture scaled by the
-    # queries; the re-searches have no capture of their own at this size
+    # queries; reported only for the captured build, leaf capacity and k
     traffic1 = (tr["bytes_per_query"] * q1
                 if tr["bytes_per_query"] and tr["src_sha"] == sha and tr["leaf_max"] == leaf
                 and tr["k"] == k else None)
@@ -267,23 +272,24 @@ def rooflines(stats, n, k, leaf, passes, step_ms, clk, device):
               "knn_requery": msr, "select": mean("ms_select"),
               "rules_other": mean("ms_rules") - mean("ms_select"),
               "total": mean("ms_total")}
-    return {"bound": "hbm", "kernel": "knn_kernel: kNN/cost search (first full pass + re-searches)",
-            "achieved": knn_ach, "peak": peak, "unit": "GB/s", "frac": knn_ach / peak,
-            "peak_kind": kind, "traffic": None,
-            "traffic_note": "no single capture covers the first pass and the re-searches; "
-                            "first_pass.traffic is the first pass's (one launch)",
-            "units": q1 + rq, "unit_name": "queries", "bytes_per_unit": bq, "ms": ms_knn,
-            "first_pass": {"queries": q1, "ms": ms1, "achieved": gbs(q1 * bq, ms1),
-                           "traffic": traffic1,
-                           "traffic_basis": "%s B per query (ncu dram read + write of the "
-                                            "first pass, one-station site scan, leaf %d) x "
-                                            "queries" % (tr["bytes_per_query"], tr["leaf_max"]),
-                           "frac": gbs(q1 * bq, ms1) / peak,
-                           "pairs_per_query": pairs / max(q1, 1),
-                           "alu": {"achieved": alu / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
-                                   "frac": alu / peak_ops, "ops_per_pair": ALU_OPS_PER_PAIR,
-                                   "peak_basis": "%d SMs x 4 x 32 lanes x %.0f MHz (median SM "
-                                                 "clock sampled)" % (sms, mhz)}},
+    return {"bound": "hbm", "kernel": "knn_kernel<8,0,0,0>: the first full kNN/cost pass (one "
+                                      "launch per step)",
+            "achieved": first_ach, "peak": peak, "unit": "GB/s", "frac": first_ach / peak,
+            "hbm_frac": first_ach / peak, "peak_kind": kind, "traffic": traffic1,
+            "traffic_basis": "%s B per query (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                             "of this kernel, one-station site scan, leaf %d, k %d) x the "
+                             "launch's queries" % (tr["bytes_per_query"], tr["leaf_max"],
+                                                   tr["k"]),
+            "units": q1, "unit_name": "queries", "bytes_per_unit": bq, "ms": ms1,
+            "pairs_per_query": pairs / max(q1, 1),
+            "binding": "alu",
+            "alu": {"achieved": alu / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                    "frac": alu / peak_ops, "ops_per_pair": ALU_OPS_PER_PAIR,
+                    "peak_basis": "%d SMs x 4 x 32 lanes x %.0f MHz (median SM clock "
+                                  "sampled)" % (sms, mhz)},
+            "knn_search": {"what": "first pass + re-searches of the removal rounds",
+                           "queries": q1 + rq, "ms": ms_knn, "achieved": knn_ach,
+                           "frac": knn_ach / peak},
             "requeries": {"queries": rq, "ms": msr, "achieved": gbs(rq * bq, msr),
                           "frac": (gbs(rq * bq, msr) or 0) / peak},
             "step": {"bytes": step_b, "achieved": step_ach, "frac": step_ach / peak,
@@ -382,18 +388,28 @@ def run_batched(args, pd, torch, dev, stream):
                         "packed_vs_single": single_ms / psub_ms}}
 
 
+def _serve_scan(spec):
+    seed, n_el = spec
+    return synth.room_scan(seed=seed, n_az=5 * n_el, n_el=n_el).xyz
+
+
 def run_serving(args, pd, torch, dev):
     """Poisson arrivals of room scans (n log-uniform in 100k-10M) at --serve-rate
     scans/s through pd_serve_*, orientation term 0.5 with network normals."""
+    import multiprocessing as mp
+
     from oracle import normals as onorm  # angle helper only (reporting)
     rng = np.random.default_rng(0)
-    # a pool of distinct scans, reused round-robin by the requests
-    sizes = np.exp(rng.uniform(np.log(1e5), np.log(1e7), args.serve_pool))
+    # one distinct scan per request (--serve-pool 0), or a pool reused
+    # round-robin; cast on the host cores (a spawned pool: this process
+    # already holds a CUDA context)
+    npool = args.serve_pool if args.serve_pool > 0 else args.serve_requests
+    sizes = np.exp(rng.uniform(np.log(1e5), np.log(1e7), npool))
+    specs = [(100 + i, max(10, int(round(np.sqrt(sz / 5.0))))) for i, sz in enumerate(sizes)]
     pool = []
-    for i, sz in enumerate(sizes):
-        n_el = max(10, int(round(np.sqrt(sz / 5.0))))
-        s = synth.room_scan(seed=100 + i, n_az=5 * n_el, n_el=n_el)
-        pool.append((pd.pinned_like(s.xyz), s.n))
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as wp:
+        for xyz in wp.imap(_serve_scan, specs, chunksize=1):
+            pool.append((pd.pinned_like(xyz), xyz.shape[0]))
     ctx = pd.Context(use_torch_allocator=False)
     # the network: trained on the PCA normals of the planar rows of one scan
     tr_scan = synth.room_scan(seed=99, n_az=1000, n_el=200)
@@ -408,14 +424,21 @@ def run_serving(args, pd, torch, dev):
                            steps=args.train_steps, batch=4096, lr=2e-3, seed=0)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    # angular error of the network against PCA on an unseen pool scan
-    x0 = torch.from_numpy(np.asarray(pool[0][0])).to(dev)
+    # angular error of the network against PCA (planar rows) and against the
+    # generator's analytic normals (every row) on an unseen scan
+    tst = synth.room_scan(seed=100, n_az=int(5 * specs[0][1]), n_el=int(specs[0][1]),
+                          normals=True)
+    x0 = torch.from_numpy(tst.xyz).to(dev)
     g = pd.Grid(ctx, x0)
     feat, pca, valid = pd.pd_normals_pca(g)
     g.free()
     u, _ = pd.pd_mlp_forward(trainer.params, feat)
     planar = ((valid & pd.PD_NORMAL_PLANAR) != 0).cpu().numpy()
-    ang = onorm.angle(u.cpu().numpy()[planar], pca.cpu().numpy()[planar])
+    un, pn = u.cpu().numpy(), pca.cpu().numpy()
+    ang = onorm.angle(un[planar], pn[planar])
+    ang_true = onorm.angle(un, tst.normals)
+    defined = (valid.cpu().numpy() & 1) != 0
+    ang_pca_true = onorm.angle(pn[defined], tst.normals[defined])
     ratio, k, w = 0.25, 4, 0.5
     leaf = args.leaf_max or pd.pd_autotune(ctx, x0, ratio, k=k, term=pd.PD_TERM_ORIENT, weight=w,
                                            normals=pd.pd_normals_mlp(ctx, trainer.params, feat,
@@ -451,9 +474,10 @@ def run_serving(args, pd, torch, dev):
     # a second stream at 70 % of the throughput the first one reached: the
     # latency of the loop when it keeps up with its arrivals
     sustain = serve_pass(0.7 * main["throughput"] / mean_n, max(20, args.serve_requests // 2))
-    # the plain single-scan path on the same pool, one scan at a time
+    # the plain single-scan path on the first scans of the pool, one at a time
+    single_pool = pool[:args.serve_compare]
     t0 = time.perf_counter()
-    for x, n in pool:
+    for x, n in single_pool:
         xd = torch.from_numpy(np.asarray(x)).to(dev)
         g = pd.Grid(ctx, xd)
         feat, pca, _ = pd.pd_normals_pca(g)
@@ -464,7 +488,7 @@ def run_serving(args, pd, torch, dev):
     single_s = time.perf_counter() - t0
     ctx.close()
     return {"workload": "%d requests, Poisson %.0f scans/s, room scans n log-uniform 100k-10M "
-                        "(pool of %d, mean %.2fM), k=%d + %.1f x orientation term, network "
+                        "(%d distinct scans, mean %.2fM), k=%d + %.1f x orientation term, network "
                         "normals, keep %g%%" % (args.serve_requests, args.serve_rate,
                                                  len(pool), np.mean([n for _, n in pool]) / 1e6,
                                                  k, w, 100 * ratio),
@@ -472,12 +496,21 @@ def run_serving(args, pd, torch, dev):
             "latency_ms": main["latency_ms"], "queue_wait_ms": main["queue_wait_ms"],
             "throughput": main["throughput"], "unit": UNIT, "offered": main["offered"],
             "sustainable": sustain,
-            "single_scan_path": {"value": sum(n for _, n in pool) / single_s,
-                                 "what": "pool scans one at a time, host-timed, inputs on device"},
+            "single_scan_path": {"value": sum(n for _, n in single_pool) / single_s,
+                                 "scans": len(single_pool),
+                                 "what": "the first scans one at a time, host-timed, inputs on "
+                                         "device"},
             "normals": {"train_steps": args.train_steps, "train_s": train_s,
                         "final_loss": float(losses[-20:].mean().item()),
                         "angle_vs_pca_deg": {"median": float(np.degrees(np.median(ang))),
-                                             "p90": float(np.degrees(np.percentile(ang, 90)))}}}
+                                             "p90": float(np.degrees(np.percentile(ang, 90))),
+                                             "rows": "planar rows"},
+                        "angle_vs_analytic_deg": {
+                            "network": {"median": float(np.degrees(np.median(ang_true))),
+                                        "p90": float(np.degrees(np.percentile(ang_true, 90)))},
+                            "pca": {"median": float(np.degrees(np.median(ang_pca_true))),
+                                    "p90": float(np.degrees(np.percentile(ang_pca_true, 90)))},
+                            "rows": "every point (PCA: where it is defined)"}}}
 
 def run_gpu(args, wl, rank, world, local_rank, dist):
     import torch
@@ -669,7 +702,10 @@ def main(argv=None):
     ap.add_argument("--batch-slots", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=50.0)
-    ap.add_argument("--serve-pool", type=int, default=12)
+    ap.add_argument("--serve-pool", type=int, default=0,
+                    help="distinct scans reused round-robin (0: one per request)")
+    ap.add_argument("--serve-compare", type=int, default=24,
+                    help="scans also run one at a time through the single-scan path")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--normals-only", action="store_true",
