@@ -20,16 +20,6 @@ namespace pd {
 
 #define BATCH_BLOCKS (device_sms() * 8)
 
-// The scan of work item w: the last i with chunk0(i) <= w (binary search).
-__device__ __forceinline__ int item_scan(const int* chunk0, int nseg, int w) {
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (chunk0[mid] <= w) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 __device__ __forceinline__ int pack_scan_of(const PackScan* sc, int nsc, int w) {
     int lo = 0, hi = nsc - 1;
     while (lo < hi) {
@@ -141,8 +131,9 @@ __global__ void seg_ranges_kernel(const int4* __restrict__ pos, int64_t ng, SegD
     if (i > 0) seg[i - 1].e = (int)lo;
 }
 
-// chunk0[i] = work items of the scans before i; one block of 1024 threads.
-__global__ void seg_chunks_kernel(const SegDev* seg, int nseg, int* chunk0) {
+// chunk0[i] = work items of the scans before i, items[w] = the scan of work
+// item w; one block of 1024 threads.
+__global__ void seg_chunks_kernel(const SegDev* seg, int nseg, int* chunk0, int* items) {
     __shared__ int part[1024];
     const int t = threadIdx.x;
     const int per = (nseg + 1023) / 1024;
@@ -166,7 +157,10 @@ __global__ void seg_chunks_kernel(const SegDev* seg, int nseg, int* chunk0) {
     int acc = t ? part[t - 1] : 0;
     for (int j = 0; j < per; j++) {
         const int i = t * per + j;
-        if (i < nseg) chunk0[i] = acc;
+        if (i < nseg) {
+            chunk0[i] = acc;
+            for (int w = 0; w < loc[j]; w++) items[acc + w] = i;
+        }
         acc += loc[j];
     }
     if (t == 1023) chunk0[nseg] = part[1023];
@@ -191,9 +185,9 @@ __global__ void seg_setup_kernel(RoundDev* rd) {
 
 // The range of work item w in pass `pass`: grid positions (pass 0) or the
 // scan's segment of the previous pass's list.  Empty for finished scans.
-__device__ __forceinline__ void seg_item(const SegDev* seg, const int* chunk0, int nseg, int w,
-                                         int pass, int& i, long long& lo, long long& hi) {
-    i = item_scan(chunk0, nseg, w);
+__device__ __forceinline__ void seg_item(const SegDev* seg, const int* chunk0, const int* items,
+                                         int w, int pass, int& i, long long& lo, long long& hi) {
+    i = items[w];
     const SegDev& s = seg[i];
     const long long off = (long long)(w - chunk0[i]) * PD_SEG_CHUNK;
     if (pass == 0) {
@@ -211,8 +205,8 @@ __device__ __forceinline__ void seg_item(const SegDev* seg, const int* chunk0, i
 __global__ void seg_hist_kernel(const u64* __restrict__ prim, const uint8_t* __restrict__ alive,
                                 const u64* __restrict__ bp0, const int* __restrict__ bi0,
                                 const u64* __restrict__ bp1, const int* __restrict__ bi1,
-                                int pass, const SegDev* seg, const int* chunk0, int nseg,
-                                uint32_t* hist) {
+                                int pass, const SegDev* seg, const int* chunk0,
+                                const int* items, int nseg, uint32_t* hist) {
     __shared__ uint32_t h[4096];
     __shared__ int s_i;
     __shared__ long long s_lo, s_hi;
@@ -223,7 +217,7 @@ __global__ void seg_hist_kernel(const u64* __restrict__ prim, const uint8_t* __r
         if (threadIdx.x == 0) {
             int i;
             long long lo, hi;
-            seg_item(seg, chunk0, nseg, w, pass, i, lo, hi);
+            seg_item(seg, chunk0, items, w, pass, i, lo, hi);
             s_i = i;
             s_lo = lo;
             s_hi = hi;
@@ -355,7 +349,7 @@ __global__ void seg_find_kernel(uint32_t* hist, int pass, RoundDev* rd, SegDev* 
 __global__ void seg_compact_kernel(const u64* __restrict__ prim, const int4* __restrict__ pos,
                                    const uint8_t* __restrict__ alive, u64* bp0, int* bi0,
                                    u64* bp1, int* bi1, int pass, SegDev* seg, const int* chunk0,
-                                   int nseg) {
+                                   const int* items, int nseg) {
     __shared__ int s_i;
     __shared__ long long s_lo, s_hi;
     const u64* lp = ((pass - 1) & 1) ? bp1 : bp0;
@@ -367,7 +361,7 @@ __global__ void seg_compact_kernel(const u64* __restrict__ prim, const int4* __r
         if (threadIdx.x == 0) {
             int i;
             long long lo, hi;
-            seg_item(seg, chunk0, nseg, w, pass, i, lo, hi);
+            seg_item(seg, chunk0, items, w, pass, i, lo, hi);
             if (seg[i].done) lo = hi = 0;  // its threshold is exact already
             s_i = i;
             s_lo = lo;
@@ -450,16 +444,16 @@ cudaError_t pack_launch_unpack(const PackScan* sc, int nsc, int nchunks, const u
     pack_unpack_kernel<<<grid_for(nchunks), 256, 0, st>>>(sc, nsc, nchunks, keep); note_launch();
     return cudaGetLastError();
 }
-cudaError_t seg_launch_ranges(const int4* pos, int64_t ng, SegDev* seg, int* chunk0, int nseg,
-                              int shift, cudaStream_t st) {
+cudaError_t seg_launch_ranges(const int4* pos, int64_t ng, SegDev* seg, int* chunk0, int* items,
+                              int nseg, int shift, cudaStream_t st) {
     if (nseg < 1 || nseg > PD_SEG_MAX) return cudaErrorInvalidValue;
     seg_ranges_kernel<<<(nseg + 1 + 255) / 256, 256, 0, st>>>(pos, ng, seg, nseg, shift); note_launch();
-    seg_chunks_kernel<<<1, 1024, 0, st>>>(seg, nseg, chunk0); note_launch();
+    seg_chunks_kernel<<<1, 1024, 0, st>>>(seg, nseg, chunk0, items); note_launch();
     return cudaGetLastError();
 }
 cudaError_t seg_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t ng,
                               SelBuffers& b, uint32_t* hist, RoundDev* rd, SegDev* seg,
-                              const int* chunk0, int nseg, cudaStream_t st) {
+                              const int* chunk0, const int* items, int nseg, cudaStream_t st) {
     if (nseg < 1 || nseg > PD_SEG_MAX) return cudaErrorInvalidValue;
     // work items: at most ng / CHUNK + nseg; the launch size depends on the
     // layout only, so a captured round replays it unchanged
@@ -467,11 +461,11 @@ cudaError_t seg_launch_select(const u64* prim, const int4* pos, const uint8_t* a
     seg_setup_kernel<<<1, 32, 0, st>>>(rd); note_launch();
     for (int pass = 0; pass < 8; pass++) {
         seg_hist_kernel<<<blocks, 256, 0, st>>>(prim, alive, b.p[0], b.i[0], b.p[1], b.i[1], pass,
-                                                seg, chunk0, nseg, hist); note_launch();
+                                                seg, chunk0, items, nseg, hist); note_launch();
         seg_find_kernel<<<nseg, 256, 0, st>>>(hist, pass, rd, seg); note_launch();
         if (pass < 7) {
             seg_compact_kernel<<<blocks, 256, 0, st>>>(prim, pos, alive, b.p[0], b.i[0], b.p[1],
-                                                       b.i[1], pass, seg, chunk0, nseg); note_launch();
+                                                       b.i[1], pass, seg, chunk0, items, nseg); note_launch();
         }
     }
     return cudaGetLastError();

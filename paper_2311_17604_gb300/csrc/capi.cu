@@ -233,6 +233,7 @@ struct pd_grid {
     int nseg = 0, seg_shift = 0;
     SegDev* seg = nullptr;
     int* seg_chunk0 = nullptr;
+    int* seg_items = nullptr;  // the scan of every selection work item
     std::vector<long long> seg_n, seg_m;  // host copies: points and targets per scan
 };
 
@@ -462,7 +463,7 @@ extern "C" const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err 
 static int grid_release(pd_grid* g) {
     void* ptrs[] = {g->pos, g->code, g->leaf, g->alive, g->rgb, g->nrm, g->hash, g->groups,
                     g->prim, g->nbr, g->rk2, g->flg, g->hz, g->d_int, g->d_u64, g->glist,
-                    g->gcount, g->cmin, g->nbr0, g->seg, g->seg_chunk0};
+                    g->gcount, g->cmin, g->nbr0, g->seg, g->seg_chunk0, g->seg_items};
     for (void* p : ptrs) gfree(g, p);
     return PD_OK;
 }
@@ -935,7 +936,7 @@ int settle_round(pd_grid* g, RoundDev* rd, const RoundDev& h, uint8_t* inP, uint
             CK(cudaMemcpyAsync(&rd->seg_rank_one, &one, sizeof(int), cudaMemcpyHostToDevice,
                                g->st));
             CK(seg_launch_select(g->prim, g->pos, g->alive, g->ng, *sel, seg_hist, rd, g->seg,
-                                 g->seg_chunk0, g->nseg, g->st));
+                                 g->seg_chunk0, g->seg_items, g->nseg, g->st));
             CK(cudaMemcpyAsync(&rd->seg_rank_one, &zero, sizeof(int), cudaMemcpyHostToDevice,
                                g->st));
             CK(seg_launch_accept(g->prim, g->pos, g->alive, g->ng, rd, inP, cand, d + 4, g->st));
@@ -1133,7 +1134,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
     }
     // packed batch: every scan's grid range and its selection work items
     if (g->nseg)
-        CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->nseg, g->seg_shift, g->st));
+        CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->seg_items, g->nseg,
+                             g->seg_shift, g->st));
     // ---- first neighbour pass
     {
         unsigned long long* dpairs;
@@ -1252,7 +1254,7 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
                 Span t(T, &g->stats.ms_select);
                 if (g->nseg)
                     CK(seg_launch_select(g->prim, g->pos, g->alive, g->ng, sb, seg_hist, rd,
-                                         g->seg, g->seg_chunk0, g->nseg, g->st));
+                                         g->seg, g->seg_chunk0, g->seg_items, g->nseg, g->st));
                 else
                     CK(round_launch_select(g->prim, g->pos, g->alive, g->ng, sb, rd, g->st));
             }
@@ -1426,8 +1428,8 @@ int decimate_impl(pd_grid* g, const pd_cost_params* cp, int64_t m, uint8_t* keep
             rc = compact_rebuild(g, true);
             if (rc) return rc;
             if (g->nseg)
-                CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->nseg, g->seg_shift,
-                                     g->st));
+                CK(seg_launch_ranges(g->pos, g->ng, g->seg, g->seg_chunk0, g->seg_items,
+                                     g->nseg, g->seg_shift, g->st));
             built = live;
         }
     }
@@ -2164,7 +2166,8 @@ int batch_packed(pd_ctx* ctx, pd_scan_desc* scans, int nscans, const pd_cost_par
     g->seg_m = mv;
     g->seg = (SegDev*)ctx_alloc(ctx, sizeof(SegDev) * nscans, st);
     g->seg_chunk0 = (int*)ctx_alloc(ctx, sizeof(int) * (nscans + 1), st);
-    if (!g->seg || !g->seg_chunk0) {
+    g->seg_items = (int*)ctx_alloc(ctx, sizeof(int) * (N / PD_SEG_CHUNK + nscans + 1), st);
+    if (!g->seg || !g->seg_chunk0 || !g->seg_items) {
         set_err(ctx, "pd_decimate_batch: allocation of the scan table failed%s", "", 0);
         return PD_ENOMEM;
     }

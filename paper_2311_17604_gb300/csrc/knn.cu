@@ -253,6 +253,23 @@ __device__ inline u64 box_d2(int ux, int uy, int uz, int bx, int by, int bz, int
     return s;
 }
 
+// The same in 32-bit arithmetic, for levels whose cell edge is at most
+// 2^13 mm: the box is the query's own or an adjacent cell's leaf, so every
+// coordinate gap is below 2 * 2^13 and the sum below 2^30.
+__device__ inline u64 box_d2_32(int ux, int uy, int uz, int bx, int by, int bz, int sh) {
+    const int q[3] = {ux, uy, uz};
+    const int c[3] = {bx, by, bz};
+    uint32_t s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int lo = c[a] * (1 << sh);
+        const int hi = (c[a] + 1) * (1 << sh) - 1;
+        const int d = q[a] < lo ? lo - q[a] : (q[a] > hi ? q[a] - hi : 0);
+        s += (uint32_t)(d * d);
+    }
+    return (u64)s;
+}
+
 // Squared distance from the query to the outside of the level-L cube of
 // cells [c-1, c+1]; ~0 when the cube holds the whole cloud.
 __device__ inline u64 gap2(const GridView& g, int ux, int uy, int uz, int L, int cx, int cy,
@@ -442,9 +459,15 @@ __device__ __forceinline__ void knn_level(const GridView& g, const KnnArgs& a, i
         u64 bd = ~0ull;
         if (todo) {
             u64 bound = top.at(R - 1);
-            bd = box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift);
+            bd = PACK ? box_d2_32(ux, uy, uz, bxr, byr, bzr, lv + g.shift)
+                      : box_d2(ux, uy, uz, bxr, byr, bzr, lv + g.shift);
             skip = bound != ~0ull && bd > bound;
         }
+        // every lane of the warp scans a range unless none needs it: the
+        // lanes that do not still fill their stored entries beyond the R
+        // nearest from it (measured: skipping per lane halves the candidates
+        // a lane takes but leaves sparser buffers, whose extra re-searches in
+        // the removal rounds cost more than the pass saves)
         if (__all_sync(FULLM, skip)) {
             if (bd < hzl) hzl = bd;
             continue;

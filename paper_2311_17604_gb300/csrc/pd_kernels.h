@@ -331,16 +331,17 @@ cudaError_t pack_launch_copy(const PackScan* sc, int nsc, int nchunks, int32_t* 
 // Every scan's keep mask from the packed one.
 cudaError_t pack_launch_unpack(const PackScan* sc, int nsc, int nchunks, const uint8_t* keep,
                                cudaStream_t st);
-// Grid ranges [b, e) of every scan and the prefix counts of their work items
-// (chunk0[0..nseg]), from the Morton-ordered positions.
-cudaError_t seg_launch_ranges(const int4* pos, int64_t ng, SegDev* seg, int* chunk0, int nseg,
-                              int shift, cudaStream_t st);
+// Grid ranges [b, e) of every scan, the prefix counts of their work items
+// (chunk0[0..nseg]) and the scan of every work item (items: ng / PD_SEG_CHUNK
+// + nseg entries at least), from the Morton-ordered positions.
+cudaError_t seg_launch_ranges(const int4* pos, int64_t ng, SegDev* seg, int* chunk0, int* items,
+                              int nseg, int shift, cudaStream_t st);
 // Per-scan selection of the round's threshold (R2): every scan's rank-th
 // largest live key, rank from its live count, target and the band.  hist:
 // nseg x 4096 words, zero on entry and on return.
 cudaError_t seg_launch_select(const u64* prim, const int4* pos, const uint8_t* alive, int64_t ng,
                               SelBuffers& b, uint32_t* hist, RoundDev* rd, SegDev* seg,
-                              const int* chunk0, int nseg, cudaStream_t st);
+                              const int* chunk0, const int* items, int nseg, cudaStream_t st);
 // cnt[scan] += flagged points of the scan.
 cudaError_t seg_launch_count(const uint8_t* flag, const int4* pos, int64_t ng, int shift,
                              unsigned long long* cnt, cudaStream_t st);

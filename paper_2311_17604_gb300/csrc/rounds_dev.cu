@@ -509,7 +509,10 @@ __global__ void __launch_bounds__(256, 6) k1d_update_kernel(BufView b, const uin
 // "Sub-sampling algorithm").  Fewer than k left: the point is searched again.
 #define UPD_SMAX 8
 
-__global__ void kkd_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
+// Held to 48 registers for 5 blocks per SM: the loop over the stored entries
+// waits on dependent loads, and the recomputation that spills runs only for
+// points that lost a neighbour.
+__global__ void __launch_bounds__(256, 5) kkd_update_kernel(BufView b, const uint8_t* __restrict__ alive, int64_t n, int S,
                                   int k, uint8_t* dirty, RoundDev* rd) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool upd = false, req = false;
@@ -584,9 +587,11 @@ __global__ void kkd_cand2_kernel(BufView b, const uint8_t* __restrict__ alive, i
             u64 ps = b.prim[s];
             int4 qs = b.pos[s];
             int is = qs.w;
-            u64 tp;
-            int ti;
-            round_tau(rd, qs, tp, ti);  // packed batch: the threshold of the point's scan
+            u64 tp = rd->tau_prim;
+            int ti = rd->tau_idx;
+            // packed batch: tp is the least threshold over the scans; a point
+            // above it takes its own scan's threshold
+            if (rd->seg && ps >= tp) round_tau(rd, qs, tp, ti);
             if (!key_gt(tp, ti, ps, is)) {
                 uint8_t fl = b.flg[s];
                 bool lower = !(fl & 1);
