@@ -648,6 +648,11 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
                          "on %d threads, greedy single-threaded; %.1f s"
                          % (nsmp, k, wl["ratio"], threads, dt)}
     batched = serving = None
+    # the batched and served legs start from an empty device: the scan and
+    # the decimation's cached blocks are released first
+    del xyz_dev, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     if world == 1 and not args.no_batch:
         batched = run_batched(args, pd, torch, dev, stream)
     if world == 1 and not args.no_serve:
