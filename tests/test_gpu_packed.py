@@ -106,6 +106,27 @@ def test_packed_colour_within_tolerance(pd, ctx, k):
         assert agree >= 0.999, agree
 
 
+def test_packed_orientation_within_tolerance(pd, ctx):
+    """The orientation term (Eq. 13, w = 1 - 0.5 (1 - |n_p . n_q|)) with the
+    generator's analytic normals, packed per scan with the coordinates."""
+    scans, clouds = [], []
+    for sp in synth.batch_specs(seed=12, count=4, n_lo=2e4, n_hi=8e4):
+        sc = synth.room_scan(seed=sp["seed"], n_az=sp["n_az"], n_el=sp["n_el"], dims=sp["dims"],
+                             scanner=sp["scanner"], normals=True)
+        scans.append((sc, sp["ratio"]))
+        clouds.append({"xyz": torch.from_numpy(sc.xyz).cuda(),
+                       "normals": torch.from_numpy(sc.normals).cuda(), "ratio": sp["ratio"]})
+    keeps, _ = pd.pd_decimate_batch(ctx, clouds, k=4, term=pd.PD_TERM_ORIENT, weight=0.5,
+                                    concurrency=pd.PD_BATCH_PACKED)
+    for (sc, q), kp in zip(scans, keeps):
+        m = oracle.target_count(sc.n, q)
+        got = kp.cpu().numpy()
+        assert int(got.sum()) == m
+        ref = oracle.decimate(sc.xyz, 4, m, term=oracle.TERM_ORIENT, a=0.5, nrm=sc.normals)
+        agree = float((got == ref).mean())
+        assert agree >= 0.999, agree
+
+
 def test_packed_fallbacks_give_alone_results(pd, ctx):
     """Not packable: a target of k points or fewer, or a scan with more
     coincident points than it must lose; the batch runs in slots."""
