@@ -214,7 +214,7 @@ ALU_OPS_PER_PAIR = 9   # 3 subtractions, 3 multiply-adds, compare, select, loop:
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a one-station
 # site scan at the leaf capacity below; reported only while the kNN sources
 # hash to src_sha and the timed run uses the same leaf capacity and k.
-KNN_TRAFFIC = {"k": 1, "leaf_max": 32, "bytes_per_query": 113.9, "src_sha": "262117e2602d3920"}
+KNN_TRAFFIC = {"k": 1, "leaf_max": 32, "bytes_per_query": 113.9, "src_sha": "35c5ffc4f79967f7"}
 KNN_SOURCES = ["paper_2311_17604_gb300/csrc/knn.cu", "paper_2311_17604_gb300/csrc/pd_internal.cuh",
                "paper_2311_17604_gb300/csrc/pd_kernels.h"]
 
@@ -350,8 +350,27 @@ def run_batched(args, pd, torch, dev, stream):
     for c, kp in zip(clouds, keeps):
         assert int(kp.sum().item()) == oracle.target_count(int(c["xyz"].shape[0]), c["ratio"])
     del keeps
-    # the comparison: the first scans through slots and one at a time
-    sub = clouds[:args.batch_compare]
+    compare = _batch_compare(args, pd, ctx, clouds[:args.batch_compare], kw, timed, stream)
+    ctx.close()
+    return {"workload": "%d room scans, sizes log-uniform 50k-5M (%d points), RGB, k=1 + 0.3 x "
+                        "colour term, keep U[5%%, 50%%]" % (len(clouds), total),
+            "mode": "packed: every scan in one grid, one launch per round kernel for all scans",
+            "scans": len(clouds), "points": total, "leaf_max": leaf,
+            "value": total / (packed_ms / 1e3), "unit": UNIT, "ms": packed_ms,
+            "rounds": stats[0]["rounds"], "gpu_launches": int(launches),
+            "phases_ms": {key: stats[0][key] for key in ("ms_grid", "ms_knn_first",
+                                                        "ms_knn_requery", "ms_select",
+                                                        "ms_danger", "ms_build", "ms_rules")},
+            "graph_rounds": stats[0]["graph_rounds"],
+            "per_scan_ms": {"p50": packed_ms, "p99": packed_ms,
+                            "what": "every scan of a packed batch finishes with the batch"},
+            "compare": compare}
+
+
+def _batch_compare(args, pd, ctx, sub, kw, timed, stream):
+    """The first scans of the batch packed, through slots and one at a time."""
+    if not sub:
+        return None
     sub_pts = sum(int(c["xyz"].shape[0]) for c in sub)
     pd.pd_decimate_batch(ctx, sub[:4], concurrency=4, stream=stream, **kw)   # warm (slots)
     (_, sstats), slots_ms = timed(lambda: pd.pd_decimate_batch(
@@ -366,26 +385,15 @@ def run_batched(args, pd, torch, dev, stream):
             g.free()
     _, single_ms = timed(single)
     per_scan = [st["ms_total"] for st in sstats]
-    ctx.close()
-    return {"workload": "%d room scans, sizes log-uniform 50k-5M (%d points), RGB, k=1 + 0.3 x "
-                        "colour term, keep U[5%%, 50%%]" % (len(clouds), total),
-            "mode": "packed: every scan in one grid, one launch per round kernel for all scans",
-            "scans": len(clouds), "points": total, "leaf_max": leaf,
-            "value": total / (packed_ms / 1e3), "unit": UNIT, "ms": packed_ms,
-            "rounds": stats[0]["rounds"], "gpu_launches": int(launches),
-            "per_scan_ms": {"p50": packed_ms, "p99": packed_ms,
-                            "what": "every scan of a packed batch finishes with the batch"},
-            "compare": {"scans": len(sub), "points": sub_pts,
-                        "packed": {"value": sub_pts / (psub_ms / 1e3), "ms": psub_ms},
-                        "slots": {"value": sub_pts / (slots_ms / 1e3), "ms": slots_ms,
-                                  "slots": args.batch_slots,
-                                  "per_scan_ms": {"p50": _pct(per_scan, 50),
-                                                  "p99": _pct(per_scan, 99),
-                                                  "what": "each scan's decimation time on its "
-                                                          "slot's stream"}},
-                        "single_scan_loop": {"value": sub_pts / (single_ms / 1e3),
-                                             "ms": single_ms},
-                        "packed_vs_single": single_ms / psub_ms}}
+    return {"scans": len(sub), "points": sub_pts,
+            "packed": {"value": sub_pts / (psub_ms / 1e3), "ms": psub_ms},
+            "slots": {"value": sub_pts / (slots_ms / 1e3), "ms": slots_ms,
+                      "slots": args.batch_slots,
+                      "per_scan_ms": {"p50": _pct(per_scan, 50), "p99": _pct(per_scan, 99),
+                                      "what": "each scan's decimation time on its slot's "
+                                              "stream"}},
+            "single_scan_loop": {"value": sub_pts / (single_ms / 1e3), "ms": single_ms},
+            "packed_vs_single": single_ms / psub_ms}
 
 
 def _serve_scan(spec):
@@ -521,6 +529,14 @@ def run_gpu(args, wl, rank, world, local_rank, dist):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.batch_only:
+        # profiling aid: the batched leg alone (no step line)
+        L = pd.lib()
+        L.pd__launch_count.restype = ctypes.c_longlong
+        print(json.dumps({"batch_only": True,
+                          "batched": run_batched(args, pd, torch, dev,
+                                                 torch.cuda.current_stream(dev))}))
+        return
     scan = wl["gen"](rank)
     n, k = scan.n, wl["k"]
     import oracle
@@ -715,6 +731,8 @@ def main(argv=None):
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--normals-only", action="store_true",
                     help="time the 16-NN/PCA pass and the network forward on the workload scan")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling aid: run the batched leg alone")
     ap.add_argument("--knn-only", action="store_true",
                     help="profiling aid: build the grid and run one full kNN/cost pass")
     args = ap.parse_args(argv)
