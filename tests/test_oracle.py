@@ -119,15 +119,18 @@ def test_fig3_configuration(orc):
 
 def test_paper_cube_count():
     """The cube example of section "Results and Discussion": 10 % of the cube
-    leaves about 45,223 points, 90.45 points per m^2 over 500 m^2.  The target
-    count rule m = floor(ratio * n) must reproduce it for n = 452,230 (the
-    "452k" input that the printed count implies)."""
+    leaves about 45,223 points, 90.45 points per m^2 over 500 m^2.  Context
+    rather than a pin: the paper prints the input only as "about 452k", so the
+    check is that the printed numbers agree with each other and with the
+    target rule m = floor(ratio * n) for an input in that range (n = 452,230
+    to 452,239 give 45,223); the rule itself is pinned by the exact-count
+    invariant and the closed forms."""
     import os
     import oracle
     path = os.path.join(os.path.dirname(__file__), "golden", "paper_cube_example.txt")
     row = [l.split() for l in open(path) if l.strip() and not l.startswith("#")][0]
     m, area, density, ratio = int(row[0]), float(row[1]), float(row[2]), float(row[3])
-    assert oracle.target_count(452230, ratio) == m
+    assert all(oracle.target_count(n, ratio) == m for n in range(452230, 452240))
     assert abs(m / area - density) < 0.005
 
 
