@@ -64,3 +64,23 @@ def test_aggregate_single_process_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate(3.0, 7, None) == (3.0, 7)
+
+
+def test_reference_arm_under_torchrun_prints_one_line(orc):
+    """`bench.py --impl reference` launched as two ranks (the driver's N > 1
+    launch): rank 0 times the oracle and prints the one JSON line, the other
+    rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0", "--workload", "room"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
