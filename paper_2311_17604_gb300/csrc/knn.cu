@@ -7,8 +7,9 @@
 // load of {x, y, z, index}), the chunk is staged in shared memory, and every
 // lane streams the whole chunk against its own query, keeping the S smallest
 // (d^2, position) pairs in registers.  Squared distances are exact integers:
-// uint32 when every coordinate difference in the searched cells is at most
-// 2^15 mm, uint64 otherwise.  A cell is skipped when its box is farther than
+// uint32 at levels whose resolved cells are at most 2^13 mm wide (every
+// coordinate difference within the 3x3x3 cells is then below 3 * 2^13, so
+// d^2 < 2^32), uint64 otherwise.  A cell is skipped when its box is farther than
 // the current bound for every lane.  Exactness: every point outside the
 // searched cube lies at least g from the query (g = distance to the cube's
 // faces); when the bound that matters is below g^2 the lane is done,
