@@ -268,12 +268,12 @@ int pd_decimate_host(pd_ctx* ctx, const int32_t* xyz_host, const uint8_t* rgb_ho
  * colour or orientation term the rounds of the batch differ from those of a
  * scan alone, so the result is the same within the tolerance those terms
  * have alone.  A scan's stats are those of the whole batch, with its own n
- * and m.  Extra device memory: the packed copy (16 B per point, 19 with
- * colours, 28 with normals) and one grid over all points.  A batch that
- * cannot be packed falls back to 8 slots (below): more than PD_BATCH_MAX_SCANS
- * scans or 2^31 - 64 points, a target of k points or fewer, a missing colour
- * or normal array, tiles beyond the coordinate range (2^25 mm), or a scan
- * with more coincident points than it must lose.
+ * and m.  Extra device memory: the packed copy and its keep mask (13 B per
+ * point, 16 with colours, 25 with normals) and one grid over all points.  A
+ * batch that cannot be packed falls back to 8 slots (below): more than
+ * PD_BATCH_MAX_SCANS scans or 2^31 - 64 points, a target of k points or
+ * fewer, a missing colour or normal array, tiles beyond the coordinate range
+ * (2^25 mm), or a scan with more coincident points than it must lose.
  *
  * concurrency >= 0: scans run through `concurrency` slots (0 = 8); each slot
  * has its own stream and host thread and runs pd_build_grid +
