@@ -88,6 +88,44 @@ def greedy_from_scratch(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None):
     return live.astype(np.uint8), order
 
 
+def rounds_r1_from_scratch(xyz, k, m):
+    """Parallel removal rounds with the rules R1 and R2 only, recomputed from
+    scratch every round (density cost): a live point p goes in a round when
+    (R2) its key is among the `need` = live - m largest, and (R1) its key
+    beats the key of every live q != p that shares a tie-inclusive k-ball
+    with it, d^2(p, q) <= r_k^2(p) or d^2(p, q) <= r_k^2(q), with r_k^2 the
+    k-th smallest squared distance to the other live points.  These are the
+    rounds of the exactness argument for k = 1; the library adds a third rule
+    (danger pairs) for k >= 2, where R1 and R2 alone can differ from the
+    sequential greedy.  Returns (keep, rounds)."""
+    x = np.asarray(xyz, dtype=np.int64)
+    live = np.ones(len(x), dtype=bool)
+    rounds = 0
+    while live.sum() > m:
+        rounds += 1
+        keys = keys_from_scratch(x, live, k)
+        ids = np.nonzero(live)[0]
+        need = len(ids) - m
+        kstar = sorted((keys[p] for p in ids), reverse=True)[need - 1]
+        d = x[ids][:, None, :] - x[ids][None, :, :]
+        d2 = (d * d).sum(axis=2)
+        np.fill_diagonal(d2, np.iinfo(np.int64).max)
+        rk = np.sort(d2, axis=1)[:, min(k, len(ids) - 1) - 1]
+        remove = []
+        for a, p in enumerate(ids):
+            if keys[p] < kstar:
+                continue
+            ok = True
+            for b, q in enumerate(ids):
+                if a != b and (d2[a, b] <= rk[a] or d2[a, b] <= rk[b]) and not keys[p] > keys[q]:
+                    ok = False
+                    break
+            if ok:
+                remove.append(p)
+        live[remove] = False  # never empty: the largest key always qualifies
+    return live.astype(np.uint8), rounds
+
+
 def greedy_orders_exhaustive(xyz, k, m):
     """All removal sequences of length n - m whose every step removes the key max.
 

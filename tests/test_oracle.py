@@ -134,6 +134,26 @@ def test_paper_cube_count():
     assert abs(m / area - density) < 0.005
 
 
+# ------------------------------------------------- the rounds' exactness argument
+def test_r1_r2_rounds_are_the_greedy_for_k1_but_not_for_k2_and_k4(orc):
+    """The reading behind the removal rounds (section "Sub-sampling
+    algorithm", the greedy of Eq. 10 / 11): rounds that remove every point
+    whose key beats all points sharing its tie-inclusive k-ball (R1), among
+    the `need` largest keys (R2), give the sequential greedy's result for
+    k = 1 on every cloud tried; for k = 2 and 4 they do not always, which is
+    why the library's rounds add the danger-pair rule R3 for k >= 2."""
+    diverged = {1: 0, 2: 0, 4: 0}
+    for k in (1, 2, 4):
+        for seed in range(60):
+            for span in (30, 300, 3000):
+                x = synth.random_cloud(seed, 60, span)
+                keep, _ = slow.rounds_r1_from_scratch(x, k, 15)
+                if not np.array_equal(keep, orc.decimate(x, k, 15)):
+                    diverged[k] += 1
+    assert diverged[1] == 0
+    assert diverged[2] > 0 and diverged[4] > 0, diverged
+
+
 # ------------------------------------------------- independent oracles
 @pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("seed,span", [(0, 25), (1, 400), (2, 8)])
