@@ -88,18 +88,26 @@ def greedy_from_scratch(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None):
     return live.astype(np.uint8), order
 
 
-def rounds_r1_from_scratch(xyz, k, m):
-    """Parallel removal rounds with the rules R1 and R2 only, recomputed from
-    scratch every round (density cost): a live point p goes in a round when
-    (R2) its key is among the `need` = live - m largest, and (R1) its key
-    beats the key of every live q != p that shares a tie-inclusive k-ball
-    with it, d^2(p, q) <= r_k^2(p) or d^2(p, q) <= r_k^2(q), with r_k^2 the
-    k-th smallest squared distance to the other live points.  These are the
-    rounds of the exactness argument for k = 1; the library adds a third rule
-    (danger pairs) for k >= 2, where R1 and R2 alone can differ from the
-    sequential greedy.  Returns (keep, rounds)."""
+def rounds_from_scratch(xyz, k, m, danger=True):
+    """Parallel removal rounds recomputed from scratch every round (density
+    cost), following the rules of the library's rounds:
+      R2  the key is among the `need` = live - m largest;
+      R1  the key beats the key of every live q != p that shares a
+          tie-inclusive k-ball with p: d^2(p, q) <= r_k^2(p) or
+          d^2(p, q) <= r_k^2(q), r_k^2 the k-th smallest squared distance to
+          the other live points;
+      R3  (danger=True) with tau the least key of the R1 and R2 candidates
+          and "low" the live points of key below tau, a candidate p is
+          rejected when some live q of larger key has d^2(q, p) < lambda(q),
+          the k-th smallest squared distance from q to a low point other than
+          q (infinite when fewer than k low points exist).
+    Every point left after the rules goes at once.  R1 and R2 alone are the
+    exactness argument for k = 1; for k >= 2 a removal can pull a point into
+    a larger key's k-ball later, which R3 rules out.  Returns (keep, rounds).
+    """
     x = np.asarray(xyz, dtype=np.int64)
     live = np.ones(len(x), dtype=bool)
+    big = np.iinfo(np.int64).max
     rounds = 0
     while live.sum() > m:
         rounds += 1
@@ -109,9 +117,9 @@ def rounds_r1_from_scratch(xyz, k, m):
         kstar = sorted((keys[p] for p in ids), reverse=True)[need - 1]
         d = x[ids][:, None, :] - x[ids][None, :, :]
         d2 = (d * d).sum(axis=2)
-        np.fill_diagonal(d2, np.iinfo(np.int64).max)
+        np.fill_diagonal(d2, big)
         rk = np.sort(d2, axis=1)[:, min(k, len(ids) - 1) - 1]
-        remove = []
+        cand = []
         for a, p in enumerate(ids):
             if keys[p] < kstar:
                 continue
@@ -121,8 +129,21 @@ def rounds_r1_from_scratch(xyz, k, m):
                     ok = False
                     break
             if ok:
-                remove.append(p)
-        live[remove] = False  # never empty: the largest key always qualifies
+                cand.append(a)
+        if danger:
+            tau = min(keys[ids[a]] for a in cand)
+            low = np.array([keys[q] < tau for q in ids])
+            lam = np.full(len(ids), big, dtype=np.int64)
+            for b, q in enumerate(ids):
+                if keys[q] >= tau:
+                    dl = np.sort(d2[b][low & (np.arange(len(ids)) != b)])
+                    if len(dl) >= k:
+                        lam[b] = dl[k - 1]
+            cand = [a for a in cand
+                    if not any(b != a and keys[q] > keys[ids[a]] and
+                               (lam[b] == big or d2[b, a] < lam[b])
+                               for b, q in enumerate(ids))]
+        live[ids[cand]] = False  # never empty: the largest key always qualifies
     return live.astype(np.uint8), rounds
 
 

@@ -135,23 +135,25 @@ def test_paper_cube_count():
 
 
 # ------------------------------------------------- the rounds' exactness argument
-def test_r1_r2_rounds_are_the_greedy_for_k1_but_not_for_k2_and_k4(orc):
+def test_removal_rounds_reproduce_the_sequential_greedy(orc):
     """The reading behind the removal rounds (section "Sub-sampling
-    algorithm", the greedy of Eq. 10 / 11): rounds that remove every point
-    whose key beats all points sharing its tie-inclusive k-ball (R1), among
-    the `need` largest keys (R2), give the sequential greedy's result for
-    k = 1 on every cloud tried; for k = 2 and 4 they do not always, which is
-    why the library's rounds add the danger-pair rule R3 for k >= 2."""
-    diverged = {1: 0, 2: 0, 4: 0}
-    for k in (1, 2, 4):
+    algorithm", the greedy of Eq. 10 / 11): rounds that remove at once every
+    point whose key beats all points sharing its tie-inclusive k-ball (R1),
+    among the `need` largest keys (R2), give the sequential greedy's retained
+    set for k = 1 on every cloud tried, but not always for k = 2 and 4; with
+    the danger-pair rule (R3) added they give it for k = 2 and 4 as well."""
+    diverged = {}
+    for k, danger in ((1, False), (2, False), (4, False), (2, True), (4, True)):
+        diverged[k, danger] = 0
         for seed in range(60):
             for span in (30, 300, 3000):
                 x = synth.random_cloud(seed, 60, span)
-                keep, _ = slow.rounds_r1_from_scratch(x, k, 15)
+                keep, _ = slow.rounds_from_scratch(x, k, 15, danger=danger)
                 if not np.array_equal(keep, orc.decimate(x, k, 15)):
-                    diverged[k] += 1
-    assert diverged[1] == 0
-    assert diverged[2] > 0 and diverged[4] > 0, diverged
+                    diverged[k, danger] += 1
+    assert diverged[1, False] == 0
+    assert diverged[2, False] > 0 and diverged[4, False] > 0, diverged
+    assert diverged[2, True] == 0 and diverged[4, True] == 0, diverged
 
 
 # ------------------------------------------------- independent oracles
