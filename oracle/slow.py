@@ -88,7 +88,7 @@ def greedy_from_scratch(xyz, k, m, term=TERM_NONE, a=0.0, rgb=None, nrm=None):
     return live.astype(np.uint8), order
 
 
-def rounds_from_scratch(xyz, k, m, danger=True):
+def rounds_from_scratch(xyz, k, m, danger=True, band=None):
     """Parallel removal rounds recomputed from scratch every round (density
     cost), following the rules of the library's rounds:
       R2  the key is among the `need` = live - m largest;
@@ -103,7 +103,10 @@ def rounds_from_scratch(xyz, k, m, danger=True):
           q (infinite when fewer than k low points exist).
     Every point left after the rules goes at once.  R1 and R2 alone are the
     exactness argument for k = 1; for k >= 2 a removal can pull a point into
-    a larger key's k-ball later, which R3 rules out.  Returns (keep, rounds).
+    a larger key's k-ball later, which R3 rules out.  band (a fraction of the
+    live points, as the library's rounds use): R2 takes the rank-th largest
+    key, rank = max(1, min(floor(band * live), need)), in place of the
+    need-th, and R3's tau is that key.  Returns (keep, rounds).
     """
     x = np.asarray(xyz, dtype=np.int64)
     live = np.ones(len(x), dtype=bool)
@@ -114,7 +117,8 @@ def rounds_from_scratch(xyz, k, m, danger=True):
         keys = keys_from_scratch(x, live, k)
         ids = np.nonzero(live)[0]
         need = len(ids) - m
-        kstar = sorted((keys[p] for p in ids), reverse=True)[need - 1]
+        rank = need if band is None else max(1, min(int(band * len(ids)), need))
+        kstar = sorted((keys[p] for p in ids), reverse=True)[rank - 1]
         d = x[ids][:, None, :] - x[ids][None, :, :]
         d2 = (d * d).sum(axis=2)
         np.fill_diagonal(d2, big)
@@ -131,7 +135,7 @@ def rounds_from_scratch(xyz, k, m, danger=True):
             if ok:
                 cand.append(a)
         if danger:
-            tau = min(keys[ids[a]] for a in cand)
+            tau = kstar if band is not None else min(keys[ids[a]] for a in cand)
             low = np.array([keys[q] < tau for q in ids])
             lam = np.full(len(ids), big, dtype=np.int64)
             for b, q in enumerate(ids):

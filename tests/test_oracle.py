@@ -156,6 +156,19 @@ def test_removal_rounds_reproduce_the_sequential_greedy(orc):
     assert diverged[2, True] == 0 and diverged[4, True] == 0, diverged
 
 
+@pytest.mark.parametrize("band", [0.01, 0.1, 0.5])
+def test_any_band_gives_the_greedy(orc, band):
+    """The library's rounds examine a band of the largest keys (a fraction
+    of the live points) and take the band's boundary as R3's tau; the band
+    changes only how many rounds run, never the retained set."""
+    for seed in range(20):
+        for span in (30, 3000):
+            x = synth.random_cloud(500 + seed, 60, span)
+            for k in (2, 4):
+                keep, _ = slow.rounds_from_scratch(x, k, 15, band=band)
+                assert np.array_equal(keep, orc.decimate(x, k, 15)), (seed, span, k)
+
+
 # ------------------------------------------------- independent oracles
 @pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("seed,span", [(0, 25), (1, 400), (2, 8)])
