@@ -156,6 +156,28 @@ def test_removal_rounds_reproduce_the_sequential_greedy(orc):
     assert diverged[2, True] == 0 and diverged[4, True] == 0, diverged
 
 
+def test_round_pins_catch_planted_mistakes(orc):
+    """The rounds pin above fails for plausible slips in the rules: R2's
+    threshold taken one rank too deep, or R3's lambda at the (k-1)-th low
+    point instead of the k-th (each planted in a copy of the function)."""
+    import inspect
+    src = inspect.getsource(slow.rounds_from_scratch)
+    plants = {"R2 one rank too deep": ("[rank - 1]", "[min(rank, len(ids) - 1)]"),
+              "lambda at the (k-1)-th": ("lam[b] = dl[k - 1]", "lam[b] = dl[max(k - 2, 0)]")}
+    for name, (good, bad) in plants.items():
+        assert src.count(good) == 1, name
+        ns = {}
+        exec(src.replace(good, bad).replace("def rounds_from_scratch", "def planted"),
+             vars(slow), ns)
+        diverged = 0
+        for seed in range(60):
+            for span in (30, 300, 3000):
+                x = synth.random_cloud(seed, 60, span)
+                keep, _ = ns["planted"](x, 2, 15, danger=True)
+                diverged += not np.array_equal(keep, orc.decimate(x, 2, 15))
+        assert diverged > 0, name
+
+
 @pytest.mark.parametrize("band", [0.01, 0.1, 0.5])
 def test_any_band_gives_the_greedy(orc, band):
     """The library's rounds examine a band of the largest keys (a fraction
